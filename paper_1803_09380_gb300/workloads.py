@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs shaped like the paper's cases.
+
+This module holds geometry, configuration numbers and seeded random draws
+only -- none of the method's arithmetic (no equilibria, no delta function, no
+collision).  Both the CUDA library's tests and the oracle's tests take their
+inputs from here, so neither side computes the other's inputs.
+
+Cases (arXiv 1803.09380):
+  * cylindrical Couette flow, section 3.1.2 (Eqs. 32-34): two concentric
+    rings of Lagrangian markers, the inner one rotating;
+  * flow past a fixed cylinder, section 3.2: one ring in a channel with an
+    equilibrium inlet, zero-gradient outlet and free-slip side walls;
+  * settling disks, section 3.3 (Eqs. 37-42): free rings in a closed box.
+Markers are spaced about one lattice unit apart along each ring; the arc
+length per marker is the ring perimeter over the marker count (Eq. 26).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PERIODIC, BOUNCEBACK, FREESLIP, INLET_EQ, OUTLET_ZEROGRAD = 0, 1, 2, 3, 4
+BODY_FIXED, BODY_PRESCRIBED, BODY_FREE = 0, 1, 2
+
+
+@dataclass
+class Body:
+    xy: np.ndarray            # (M, 2) marker positions, lattice units
+    ds: np.ndarray            # (M,) arc length per marker
+    kind: int = BODY_FIXED
+    xc: tuple = (0.0, 0.0)
+    u: tuple = (0.0, 0.0)
+    omega: float = 0.0
+    theta: float = 0.0
+    rho_s: float = 1.0
+    rho_f: float = 1.0
+    volume: float = 0.0
+    inertia: float = 0.0
+    radius: float = 0.0
+    gravity: tuple = (0.0, 0.0)
+
+    def as_kwargs(self) -> dict:
+        return dict(kind=self.kind, xc=self.xc, u=self.u, omega=self.omega,
+                    theta=self.theta, rho_s=self.rho_s, rho_f=self.rho_f,
+                    volume=self.volume, inertia=self.inertia, radius=self.radius,
+                    gravity=self.gravity)
+
+
+@dataclass
+class Case:
+    name: str
+    nx: int
+    ny: int
+    tau: float
+    rho0: float = 1.0
+    bc: tuple = (PERIODIC,) * 4
+    wall_u: tuple = (0.0,) * 8
+    inlet_u: tuple = (0.0, 0.0)
+    n_corr: int = 10
+    bodies: list = field(default_factory=list)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_markers(self) -> int:
+        return sum(b.xy.shape[0] for b in self.bodies)
+
+
+def ring(xc: float, yc: float, radius: float, count: int | None = None,
+         phase: float = 0.0):
+    """Markers on a circle at angles 2 pi l / M + phase, M = round(2 pi R)
+    unless given; returns (xy, ds) with ds = 2 pi R / M."""
+    m = int(round(2.0 * math.pi * radius)) if count is None else int(count)
+    ang = 2.0 * math.pi * np.arange(m) / m + phase
+    xy = np.stack([xc + radius * np.cos(ang), yc + radius * np.sin(ang)], axis=1)
+    ds = np.full(m, 2.0 * math.pi * radius / m)
+    return xy, ds
+
+
+def couette(n: int, r1: float | None = None, r2: float | None = None,
+            wall_speed: float = 0.01, tau: float = 0.8, n_corr: int = 10,
+            center: tuple | None = None) -> Case:
+    """Cylindrical Couette flow on an n x n periodic lattice: inner ring of
+    radius r1 (default 0.156 n) turning with tangential speed ``wall_speed``,
+    outer ring of radius r2 (default 0.39 n) at rest (section 3.1.2)."""
+    r1 = 0.156 * n if r1 is None else float(r1)
+    r2 = 0.39 * n if r2 is None else float(r2)
+    cx, cy = (n / 2.0, n / 2.0) if center is None else center
+    xy1, ds1 = ring(cx, cy, r1)
+    xy2, ds2 = ring(cx, cy, r2)
+    inner = Body(xy1, ds1, BODY_FIXED, xc=(cx, cy), omega=wall_speed / r1, radius=r1)
+    outer = Body(xy2, ds2, BODY_FIXED, xc=(cx, cy), omega=0.0, radius=r2)
+    return Case(f"couette{n}", n, n, tau, n_corr=n_corr, bodies=[inner, outer],
+                meta=dict(r1=r1, r2=r2, cx=cx, cy=cy, wall_speed=wall_speed))
+
+
+def couette_64() -> Case:
+    """The 64 x 64 case with radii 10 and 25 centred at (32, 32)."""
+    return couette(64, 10.0, 25.0, center=(32.0, 32.0))
+
+
+def couette_analytic(case: Case, x: np.ndarray, y: np.ndarray):
+    """Eq. 34 for the Couette case: steady (u_x, u_y) at points (x, y);
+    rigid rotation inside r1 and rest outside r2 (the fictitious fluid)."""
+    m = case.meta
+    r1, r2, U = m["r1"], m["r2"], m["wall_speed"]
+    dx, dy = x - m["cx"], y - m["cy"]
+    r = np.hypot(dx, dy)
+    w1 = U / r1
+    R = r1 / r2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ut = (r1 ** 2 - R ** 2 * r ** 2) * w1 / ((1.0 - R ** 2) * r)
+    ut = np.where(r < r1, w1 * r, np.where(r > r2, 0.0, ut))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        sx = np.where(r > 0, -dy / r, 0.0)
+        sy = np.where(r > 0, dx / r, 0.0)
+    return ut * sx, ut * sy
+
+
+def cylinder(nx: int = 1600, ny: int = 800, diameter: float = 40.0,
+             center: tuple = (400.0, 400.0), u_in: float = 0.05,
+             re: float = 20.0, markers: int = 126, n_corr: int = 10) -> Case:
+    """Flow past a fixed cylinder: equilibrium inlet at -x, zero-gradient
+    outlet at +x, free-slip walls at +-y; tau from Re = U D / nu with the
+    lattice viscosity nu = (tau - 1/2) / 3 (Eq. 8)."""
+    nu = u_in * diameter / re
+    tau = 0.5 + 3.0 * nu
+    xy, ds = ring(center[0], center[1], diameter / 2.0, count=markers)
+    body = Body(xy, ds, BODY_FIXED, xc=center, radius=diameter / 2.0)
+    return Case(f"cylinder{nx}x{ny}_re{re:g}", nx, ny, tau,
+                bc=(INLET_EQ, OUTLET_ZEROGRAD, FREESLIP, FREESLIP),
+                inlet_u=(u_in, 0.0), n_corr=n_corr, bodies=[body],
+                meta=dict(diameter=diameter, u_in=u_in, re=re))
+
+
+def disk(xc: float, yc: float, diameter: float, density_ratio: float,
+         gravity: float, kind: int = BODY_FREE) -> Body:
+    """A free rigid disk (section 3.3): area V = pi D^2 / 4, mass rho_s V,
+    moment of inertia M D^2 / 8, fluid density 1, gravity along -y."""
+    r = diameter / 2.0
+    xy, ds = ring(xc, yc, r)
+    vol = math.pi * diameter ** 2 / 4.0
+    mass = density_ratio * vol
+    return Body(xy, ds, kind, xc=(xc, yc), rho_s=density_ratio, rho_f=1.0,
+                volume=vol, inertia=mass * diameter ** 2 / 8.0, radius=r,
+                gravity=(0.0, -gravity))
+
+
+def settling_single(nx: int = 200, ny: int = 600, diameter: float = 20.0,
+                    density_ratio: float = 1.5, gravity: float = 2.0e-5,
+                    tau: float = 0.8) -> Case:
+    """One disk settling in a closed bounce-back box."""
+    b = disk(nx / 2.0 + 0.1 * diameter, ny - 3.0 * diameter, diameter,
+             density_ratio, gravity)
+    return Case(f"settle1_{nx}x{ny}", nx, ny, tau, bc=(BOUNCEBACK,) * 4,
+                bodies=[b], meta=dict(diameter=diameter))
+
+
+def settling_pair(nx: int = 200, ny: int = 800, diameter: float = 20.0,
+                  density_ratio: float = 1.01, gravity: float = 1.0e-4,
+                  tau: float = 0.8) -> Case:
+    """Two disks stacked 2 D apart with a 0.1 D lateral offset (drafting,
+    kissing, tumbling)."""
+    top = disk(nx / 2.0 - 0.1 * diameter, ny - 4.0 * diameter, diameter,
+               density_ratio, gravity)
+    low = disk(nx / 2.0, ny - 6.0 * diameter, diameter, density_ratio, gravity)
+    return Case(f"settle2_{nx}x{ny}", nx, ny, tau, bc=(BOUNCEBACK,) * 4,
+                bodies=[top, low], meta=dict(diameter=diameter))
+
+
+def shear_wave(nx: int, ny: int, amplitude: float = 0.01, mode: int = 1,
+               background=(0.0, 0.0)):
+    """Macroscopic fields of a shear wave u_x(y) = A sin(2 pi k y / ny) on a
+    uniform background: returns (rho, u_x, u_y) arrays of shape (ny, nx)."""
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    ux = background[0] + amplitude * np.sin(2.0 * math.pi * mode * y / ny)
+    uy = np.full((ny, nx), float(background[1]))
+    rho = np.ones((ny, nx))
+    return rho, ux, uy
+
+
+def random_fields(nx: int, ny: int, seed: int, du: float = 0.02,
+                  drho: float = 0.01):
+    """Seeded random smooth-ish macroscopic fields around rest."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + drho * rng.standard_normal((ny, nx))
+    ux = du * rng.standard_normal((ny, nx))
+    uy = du * rng.standard_normal((ny, nx))
+    return rho, ux, uy
+
+
+def random_perturbation(nx: int, ny: int, seed: int, amplitude: float = 1e-3):
+    """Seeded random array of shape (9, ny, nx) to add to populations."""
+    rng = np.random.default_rng(seed)
+    return amplitude * rng.standard_normal((9, ny, nx))
