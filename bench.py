@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Throughput of the IB-LBM step on one GB300: million lattice updates per
+second (MLUPS) of the full step -- the 10-iteration distribution-function
+correction (arXiv 1803.09380, Eqs. 22-29) plus the fused BGK collide + AA
+stream -- on the 4096 x 4096 cylindrical Couette lattice (radii 0.156 N and
+0.39 N, 4015 + 10037 markers, tau = 0.8, inner wall speed 0.01), FP32.
+
+One benchmark step is one time step of the method.  The lattice (604 MB in
+FP32) is larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (under torchrun) every rank runs its own independent lattice
+(replicas: the method has no cross-lattice exchange), timing is the max over
+ranks and the value is the aggregate.  --impl reference times the FP64 CPU
+oracle on the host cores instead (a bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (D2Q9+IB correction) vs HBM roofline; batched solves/s, p50/p99 latency"
+BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32", "bf16": "bf16-storage/f32"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=4096)
+    p.add_argument("--prec", choices=list(BYTES_PER_POP), default="fp32")
+    p.add_argument("--n-corr", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-budget", type=float, default=20.0,
+                   help="seconds of oracle work for the cpu_baseline sample")
+    return p.parse_args()
+
+
+def workload_config(args, case):
+    return {
+        "workload": f"cylindrical Couette {case.nx}x{case.ny}, D2Q9 BGK tau={case.tau}, "
+                    f"radii {case.meta['r1']:.3f}/{case.meta['r2']:.3f}, "
+                    f"{case.n_markers} markers, {args.n_corr} correction iterations, {args.prec}",
+        "nx": case.nx, "ny": case.ny, "markers": case.n_markers, "n_corr": args.n_corr,
+        "precision": args.prec,
+        "l2": "inputs larger than L2 (populations %.0f MB > 129 MB), no flush"
+              % (9 * case.nx * case.ny * BYTES_PER_POP[args.prec] / 1e6),
+    }
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9 or parts[0] != str(self.idx):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle timing
+def time_oracle(n: int, steps: int, n_corr: int):
+    import oracle
+    from paper_1803_09380_gb300 import workloads as wl
+    case = wl.couette(n, n_corr=n_corr)
+    L = oracle.Lattice(case.nx, case.ny, case.tau, n_corr=case.n_corr)
+    for b in case.bodies:
+        L.add_body(b.xy, b.ds, **b.as_kwargs())
+    t = time.perf_counter()
+    L.step(steps)
+    dt = time.perf_counter() - t
+    L.close()
+    return dt
+
+
+def oracle_sample(budget_s: float, n_max: int, n_corr: int, steps_hint: int = 1):
+    """Pick the largest Couette size (<= n_max, halving) whose oracle step
+    fits the budget, from a calibration on 128^2; returns (n, steps)."""
+    per_node = time_oracle(128, 2, n_corr) / (2 * 128 * 128)
+    n = n_max
+    while n > 64 and per_node * n * n * steps_hint > budget_s:
+        n //= 2
+    steps = max(1, int(budget_s / (per_node * n * n)))
+    return n, min(steps, 1000)
+
+
+def cpu_baseline(args):
+    n, steps = oracle_sample(args.cpu_budget, args.n, args.n_corr)
+    dt = time_oracle(n, steps, args.n_corr)
+    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, one thread, Couette {n}x{n} (same geometry scaled), "
+                      f"{steps} step(s), {args.n_corr} correction iterations, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1803_09380_gb300 import workloads as wl
+    case = wl.couette(args.n, n_corr=args.n_corr)
+    total = args.steps + args.warmup
+    n, _ = oracle_sample(150.0 / max(total, 1), args.n, args.n_corr)
+    import oracle
+    c = wl.couette(n, n_corr=args.n_corr)
+    L = oracle.Lattice(c.nx, c.ny, c.tau, n_corr=c.n_corr)
+    for b in c.bodies:
+        L.add_body(b.xy, b.ds, **b.as_kwargs())
+    L.step(args.warmup)
+    t = time.perf_counter()
+    L.step(args.steps)
+    dt = time.perf_counter() - t
+    value = n * n * args.steps / dt / 1e6
+    sample = (f"FP64 C oracle, one thread; each step one time step of the Couette lattice "
+              f"scaled to {n}x{n} (same geometry, {args.n_corr} correction iterations)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, case),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank, dist):
+    import numpy as np
+    import torch
+    from paper_1803_09380_gb300 import ibm
+    from paper_1803_09380_gb300 import workloads as wl
+
+    torch.cuda.set_device(local_rank)
+    case = wl.couette(args.n, n_corr=args.n_corr)
+    N2 = case.nx * case.ny
+    lat = ibm.Lattice.from_case(case, prec=args.prec, device=local_rank)
+    stream = lat._stream
+    flags = ibm.STEP_TIME_KERNELS | ibm.STEP_NO_MACRO
+
+    lat.step(max(args.warmup, 3), flags)
+    lat.sync()
+    lat.kernel_times()
+    l0, _ = lat.counters()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    barrier()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps, flags)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    k1_ms, k1_n = lat.kernel_times()
+    l1, _ = lat.counters()
+    launches = l1 - l0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N2 * args.steps * world / (ms * 1e-3) / 1e6
+
+    peak, peak_src = measured_peak_hbm()
+    bytes_per_update = 18 * BYTES_PER_POP[args.prec]
+    k1_avg_s = (k1_ms / max(k1_n, 1)) * 1e-3
+    achieved = bytes_per_update * N2 / k1_avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "collide_stream (k_even/k_odd)",
+                "peak_source": f"hbm_gbs of {peak_src} (MEASURED_PEAKS.json)",
+                "bytes_per_launch": bytes_per_update * N2,
+                "avg_launch_us": k1_avg_s * 1e6, "launches_timed": k1_n,
+                "step_frac": (bytes_per_update * N2 * args.steps / (ms * 1e-3) / 1e9) / peak}
+    lat.close()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, case, local_rank, dist, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE[args.prec], "data": "synthetic",
+                "config": workload_config(args, case), "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, case, local_rank, dist, world):
+    """The whole job through the public API: create the lattice, upload the
+    markers from pinned host memory, run the timed number of steps, read the
+    corrected density and velocity back into pinned host memory."""
+    import numpy as np
+    import torch
+    from paper_1803_09380_gb300 import ibm
+
+    nx, ny = case.nx, case.ny
+    pinned = []
+    for b in case.bodies:
+        t = torch.empty((b.xy.shape[0], 3), dtype=torch.float64, pin_memory=True)
+        t[:, :2] = torch.from_numpy(b.xy)
+        t[:, 2] = torch.from_numpy(b.ds)
+        pinned.append(t)
+    outs = [torch.empty((ny, nx), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    h2d = sum(t.numel() * 8 for t in pinned)
+    d2h = sum(t.numel() * 8 for t in outs)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat = ibm.Lattice(nx, ny, case.tau, case.rho0, args.prec, case.bc, case.wall_u, case.inlet_u,
+                      case.n_corr, device=local_rank)
+    for b, t in zip(case.bodies, pinned):
+        a = t.numpy()
+        lat.add_markers(np.ascontiguousarray(a[:, :2]), np.ascontiguousarray(a[:, 2]), **b.as_kwargs())
+    lat.step(args.steps)
+    for fld, o in zip((ibm.FIELD_RHO, ibm.FIELD_UX, ibm.FIELD_UY), outs):
+        lat.read(fld, out=o.numpy())
+    dt = time.perf_counter() - t0
+    lat.close()
+    if dist is not None:
+        tt = torch.tensor([dt], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    return {"value": nx * ny * args.steps * world / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "wall_s": dt,
+            "what": "create lattice + upload markers (pinned) + steps + read rho, ux, uy (pinned)"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_ours(args, rank, world, local_rank, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * ibm.h -- C ABI of the GB300 (sm_103a) distribution-function-correction
+ * immersed-boundary lattice Boltzmann library (arXiv 1803.09380).
+ *
+ * The library advances a D2Q9 BGK lattice (section 2.1, Eqs. 1, 3, 4, 7)
+ * whose no-slip boundaries are immersed Lagrangian markers enforced by the
+ * paper's iterative distribution-function correction (section 2.3,
+ * Eqs. 22-28, with the 4-point delta function of Eq. 15c), sums the
+ * corrections into body force and torque (Eq. 29, Eqs. 37-38) and moves
+ * free bodies with an FP64 Newton-Euler update (Eqs. 39-42).
+ *
+ * Conventions for every entry point:
+ *   - All arrays passed in or out are HOST memory, FP64, caller-owned; the
+ *     library copies inputs before returning.  Device memory is owned by the
+ *     library (plain cudaMalloc, or the allocator installed with
+ *     ibm_set_allocator) and released by ibm_destroy.
+ *   - Work is enqueued on the CUDA stream named in the lattice descriptor
+ *     (NULL = the legacy default stream).  ibm_step returns once the work is
+ *     enqueued; ibm_read_fields synchronises that stream, so asynchronous
+ *     device errors surface there (and in ibm_destroy / ibm_sync).
+ *   - No exception crosses the ABI.  Every call returns an ibm_status;
+ *     ibm_last_error(h) gives a message for the last failure on that handle
+ *     (ibm_last_error(NULL) for a failed ibm_create_lattice).
+ *   - A handle is not thread-safe: use one handle per host thread / stream.
+ *   - Lattice units throughout: dx = dt = 1, c_s^2 = 1/3.  Node (x, y) sits
+ *     at integer coordinates 0 <= x < nx, 0 <= y < ny.  Half-way walls sit
+ *     at x = -1/2, nx - 1/2, y = -1/2, ny - 1/2.
+ *   - Field arrays are row-major [ny][nx] (x fastest); populations are
+ *     [9][ny][nx] in the order e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0)
+ *     e4=(0,-1) e5=(1,1) e6=(-1,1) e7=(-1,-1) e8=(1,-1) (the rows of the
+ *     transform matrix of Eq. 5).
+ */
+#ifndef IBM_H_
+#define IBM_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IBM_ABI_VERSION 1
+
+typedef struct ibm_ctx *ibm_handle; /* opaque, library-owned */
+
+typedef enum {
+  IBM_OK = 0,
+  IBM_ERR_INVALID = 1,        /* bad argument or unsupported combination */
+  IBM_ERR_NOMEM = 2,          /* device or host allocation failed */
+  IBM_ERR_CUDA = 3,           /* a CUDA call failed (message has details) */
+  IBM_ERR_BOUNDS = 4,         /* a device-side capacity or bounds check tripped */
+  IBM_ERR_DIVERGED = 5,       /* NaN/Inf found by the watchdog */
+  IBM_ERR_TIMEOUT = 6,        /* a bounded device wait ran out */
+  IBM_WARN_NOT_CONVERGED = 7  /* corr_tol > 0 and the residual stayed above it */
+} ibm_status;
+
+/* Storage / arithmetic precision of the populations.  FP64: stored and
+ * computed in double.  FP32: stored and computed in float.  FP16_DEV and
+ * BF16_DEV: f_i - w_i stored in 16 bits, arithmetic in float.  Body force,
+ * torque and the Newton-Euler update are FP64 in every mode. */
+typedef enum { IBM_FP64 = 0, IBM_FP32 = 1, IBM_FP16_DEV = 2, IBM_BF16_DEV = 3 } ibm_precision;
+
+/* Rule at each domain side.  PERIODIC must be paired on opposite sides.
+ * INLET_EQ is supported on the -x side only (column 0 held at
+ * f^eq(rho0, inlet_u)); OUTLET_ZEROGRAD on the +x side only (populations
+ * entering column nx-1 from outside copied from column nx-2). */
+typedef enum {
+  IBM_BC_PERIODIC = 0,
+  IBM_BC_BOUNCEBACK = 1,      /* half-way bounce-back, optional wall velocity */
+  IBM_BC_FREESLIP = 2,        /* specular reflection */
+  IBM_BC_INLET_EQ = 3,
+  IBM_BC_OUTLET_ZEROGRAD = 4
+} ibm_bc;
+
+enum { IBM_SIDE_XMIN = 0, IBM_SIDE_XMAX = 1, IBM_SIDE_YMIN = 2, IBM_SIDE_YMAX = 3 };
+
+typedef struct {
+  int nx, ny;                 /* lattice size, 4 <= nx, ny; nx*ny < 2^31 */
+  double tau;                 /* BGK relaxation time, > 0.5 (nu = (tau - 1/2)/3, Eq. 8) */
+  double rho0;                /* reference density: initial state, inlet, walls */
+  int prec;                   /* ibm_precision */
+  int bc[4];                  /* ibm_bc per side, indexed by IBM_SIDE_* */
+  double wall_u[4][2];        /* velocity of each bounce-back side */
+  double inlet_u[2];          /* inlet velocity */
+  int n_corr;                 /* correction iterations N per step (paper: about 10) */
+  double corr_tol;            /* 0: always N iterations; > 0: report
+                                 IBM_WARN_NOT_CONVERGED when r^N > corr_tol */
+  int delta_points;           /* 4 (Eq. 15c); other kernels are not built */
+  void *cuda_stream;          /* cudaStream_t to enqueue on; NULL = default */
+  int device;                 /* CUDA device ordinal */
+} ibm_lattice_desc;
+
+typedef enum { IBM_BODY_FIXED = 0, IBM_BODY_PRESCRIBED = 1, IBM_BODY_FREE = 2 } ibm_body_kind;
+
+/* A rigid body carrying markers.  FIXED: markers never move; their velocity
+ * is u + omega x (X - xc) (e.g. a cylinder spinning in place).
+ * PRESCRIBED: markers move rigidly with the constant (u, omega).
+ * FREE: (u, omega) evolve by Eqs. 37-42 with the force and torque summed
+ * from the corrections (Eq. 29), the internal-mass terms, the collision
+ * force of Eq. 39 and the net weight M (1 - rho_f/rho_s) g. */
+typedef struct {
+  int kind;                   /* ibm_body_kind */
+  double xc[2];               /* mass centre */
+  double u[2];                /* translational velocity */
+  double omega;               /* angular velocity (counter-clockwise) */
+  double theta;               /* orientation angle */
+  double rho_s, rho_f;        /* solid and fluid densities */
+  double volume, inertia;     /* area V_s and moment of inertia I_s (2-D) */
+  double radius;              /* collision radius for Eq. 39 */
+  double gravity[2];          /* gravitational acceleration vector */
+} ibm_body_desc;
+
+/* Field selectors for ibm_read_fields / ibm_write_fields. */
+enum {
+  IBM_FIELD_RHO = 1,          /* [ny][nx] density of the last corrected state */
+  IBM_FIELD_UX = 2,           /* [ny][nx] velocity x of the last corrected state */
+  IBM_FIELD_UY = 3,           /* [ny][nx] velocity y of the last corrected state */
+  IBM_FIELD_F = 4,            /* [9][ny][nx] post-stream populations (read/write) */
+  IBM_FIELD_BODIES = 5,       /* [nbodies][9]: xc, yc, ux, uy, omega, theta, Fx, Fy, T */
+  IBM_FIELD_RESIDUAL = 6,     /* [n_corr + 1]: r^0..r^N of the last step */
+  IBM_FIELD_MARKERS = 7,      /* [nmarkers][2]: current marker positions */
+  IBM_FIELD_MACRO_INIT = 8    /* write only, [3][ny][nx] rho, ux, uy: f := f^eq(rho, u) */
+};
+
+/* Flags for ibm_step. */
+enum {
+  IBM_STEP_DEFAULT = 0,
+  IBM_STEP_NO_GRAPH = 1,      /* launch kernel by kernel instead of replaying a CUDA graph */
+  IBM_STEP_TIME_KERNELS = 2,  /* bracket each collide+stream launch with CUDA events */
+  IBM_STEP_NO_MACRO = 4       /* do not write rho, u on the last step of the call */
+};
+
+/* Creates a lattice in the rest equilibrium f_i = w_i rho0 (Eq. 3 with
+ * u = 0) on desc->device.  Returns IBM_ERR_INVALID for nx or ny < 4, tau
+ * <= 0.5 or not finite, an unpaired periodic side, an inlet/outlet on an
+ * unsupported side, n_corr < 0 or delta_points != 4; IBM_ERR_NOMEM or
+ * IBM_ERR_CUDA when device set-up fails.  *out is NULL on failure. */
+ibm_status ibm_create_lattice(const ibm_lattice_desc *desc, ibm_handle *out);
+
+/* Adds one rigid body and its n markers (section 2.2: the boundary is
+ * discretised into Lagrangian points).  xy: 2n doubles, interleaved
+ * (X0, Y0, X1, Y1, ...).  ds: n arc lengths per marker (Eq. 26), or NULL
+ * for an equal share of the polygon perimeter through the markers.
+ * body: its description; *body_id_out (optional) receives its index.
+ * Markers whose 4 x 4 delta-function support leaves a non-periodic side,
+ * or touches an inlet/outlet column, give IBM_ERR_INVALID. */
+ibm_status ibm_add_markers(ibm_handle h, const double *xy, const double *ds,
+                           int n, const ibm_body_desc *body, int *body_id_out);
+
+/* Advances nsteps time steps.  One step: the N-iteration correction loop on
+ * the post-stream state (Eqs. 22-28; residuals r^0..r^N recorded), body
+ * force and torque (Eq. 29), the body update (Eqs. 37-42) and marker motion,
+ * then the fused BGK collide + AA-pattern stream over every node. */
+ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags);
+
+/* Copies a field into host_dst (n_elems doubles, which must equal the
+ * field's size) after synchronising the handle's stream. */
+ibm_status ibm_read_fields(ibm_handle h, int field, double *host_dst, size_t n_elems);
+
+/* Writes IBM_FIELD_F (raw post-stream populations) or IBM_FIELD_MACRO_INIT
+ * (equilibrium of the given rho, u) from host_src, n_elems doubles. */
+ibm_status ibm_write_fields(ibm_handle h, int field, const double *host_src, size_t n_elems);
+
+/* Blocks until the handle's queued work is done; reports device errors. */
+ibm_status ibm_sync(ibm_handle h);
+
+/* Total device time of the collide+stream launches bracketed since the last
+ * call (IBM_STEP_TIME_KERNELS), in milliseconds, and their count; resets
+ * the accumulators.  Synchronises the stream. */
+ibm_status ibm_kernel_times(ibm_handle h, double *ms_total, int *launches);
+
+/* Sizes: nodes, markers, bodies, band nodes (distinct nodes inside some
+ * marker support) of the current state; any pointer may be NULL. */
+ibm_status ibm_get_sizes(ibm_handle h, long long *nodes, int *markers, int *bodies,
+                         int *band_nodes);
+
+/* Counters since creation: CUDA kernels the library enqueued for ibm_step
+ * (a CUDA-graph replay counts the kernels it contains) and time steps taken.
+ * Either pointer may be NULL. */
+ibm_status ibm_get_counters(ibm_handle h, long long *kernel_launches, long long *steps);
+
+/* Frees every device and host resource of h (NULL is a no-op). */
+ibm_status ibm_destroy(ibm_handle h);
+
+/* Message for the last failure on h (thread-local for h == NULL). */
+const char *ibm_last_error(ibm_handle h);
+
+/* Optional process-wide device allocator used for every later allocation:
+ * alloc(bytes, device, stream, ctx) returns a device pointer or NULL;
+ * release(ptr, device, stream, ctx) frees it.  Pass NULLs to go back to
+ * cudaMalloc / cudaFree.  Not thread-safe with concurrent handle creation. */
+typedef void *(*ibm_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
+typedef void (*ibm_free_fn)(void *ptr, int device, void *stream, void *ctx);
+ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn release, void *ctx);
+
+/* ABI version the library was built with (IBM_ABI_VERSION). */
+int ibm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_H_ */

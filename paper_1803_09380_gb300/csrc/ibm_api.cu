@@ -1,0 +1,658 @@
+// ibm_api.cu -- the C ABI of include/ibm.h: argument checks, device
+// allocation, the per-step launch sequence and its CUDA-graph replay, and
+// field transfers.  Every entry point catches C++ exceptions and returns a
+// status; none lets one cross the ABI.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ibm_internal.h"
+
+using namespace ibm;
+
+struct ibm_ctx : public Ctx {};
+
+namespace {
+
+ibm_alloc_fn g_alloc = nullptr;
+ibm_free_fn g_free = nullptr;
+void* g_actx = nullptr;
+thread_local std::string t_err;
+
+constexpr int kEventPairs = 4096;
+
+ibm_status fail(Ctx* h, ibm_status st, const std::string& msg) {
+  if (h) h->err = msg; else t_err = msg;
+  return st;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+void* dev_alloc(Ctx& h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (g_alloc) {
+    p = g_alloc(bytes, h.device, (void*)h.stream, g_actx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h.allocs.push_back(p);
+  return p;
+}
+
+void dev_free(Ctx& h, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < h.allocs.size(); ++k)
+    if (h.allocs[k] == p) { h.allocs.erase(h.allocs.begin() + k); break; }
+  if (g_free) g_free(p, h.device, (void*)h.stream, g_actx);
+  else cudaFree(p);
+}
+
+#define IBM_CK(h, call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      cudaGetLastError();                                                            \
+      return fail(h, IBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                \
+  } while (0)
+
+#define IBM_ALLOC(h, ptr, type, count)                                               \
+  do {                                                                               \
+    (ptr) = (type)dev_alloc(*(h), sizeof(*(ptr)) * (size_t)(count));                  \
+    if (!(ptr)) return fail(h, IBM_ERR_NOMEM, "device allocation of " #ptr " failed"); \
+  } while (0)
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+void destroy_graphs(Ctx& h) {
+  for (int p = 0; p < 2; ++p)
+    for (int m = 0; m < 2; ++m)
+      if (h.graph[p][m]) { cudaGraphExecDestroy(h.graph[p][m]); h.graph[p][m] = nullptr; }
+}
+
+ibm_status check_device_flags(Ctx* h) {
+  if (!h->dctr) return IBM_OK;
+  int ctr[2] = {0, 0};
+  IBM_CK(h, cudaMemcpyAsync(ctr, h->dctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
+  IBM_CK(h, cudaStreamSynchronize(h->stream));
+  if (ctr[1] & ERR_BAND_CAP) return fail(h, IBM_ERR_BOUNDS, "band node capacity exceeded");
+  if (ctr[1] & ERR_LIST_CAP)
+    return fail(h, IBM_ERR_BOUNDS, "more than 32 markers cover one node (markers too dense)");
+  return IBM_OK;
+}
+
+ibm_status sync_stream(Ctx* h) {
+  IBM_CK(h, cudaStreamSynchronize(h->stream));
+  IBM_CK(h, cudaGetLastError());
+  return check_device_flags(h);
+}
+
+ibm_status ensure_io(Ctx* h, size_t doubles) {
+  if (h->io_cap >= doubles) return IBM_OK;
+  if (h->dio) { IBM_CK(h, cudaStreamSynchronize(h->stream)); dev_free(*h, h->dio); h->dio = nullptr; }
+  IBM_ALLOC(h, h->dio, double*, doubles);
+  h->io_cap = doubles;
+  return IBM_OK;
+}
+
+// The launch sequence of one time step (ordering on one stream).
+void enqueue_step(Ctx& h, int parity, bool macro, bool timing) {
+  launch_ib_loop(h, parity, h.stream);
+  launch_body_update(h, h.stream);
+  if (timing && h.ev_used < kEventPairs) cudaEventRecord(h.ev[2 * h.ev_used], h.stream);
+  launch_collide_stream(h, parity, macro, h.stream);
+  if (timing && h.ev_used < kEventPairs) { cudaEventRecord(h.ev[2 * h.ev_used + 1], h.stream); h.ev_used++; }
+}
+
+ibm_status fold_events(Ctx* h) {
+  if (h->ev_used == 0) return IBM_OK;
+  IBM_CK(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < h->ev_used; ++k) {
+    float ms = 0.f;
+    IBM_CK(h, cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]));
+    h->acc_ms += ms;
+  }
+  h->acc_n += h->ev_used;
+  h->ev_used = 0;
+  return IBM_OK;
+}
+
+ibm_status upload_markers(Ctx* h) {
+  Ctx& c = *h;
+  const int M = c.nm;
+  // release the previous marker-sized buffers
+  void* olds[] = {c.dX, c.dY, c.dds, c.ddX, c.ddY, c.dmbody, c.dUx, c.dUy, c.dW, c.dnode_of,
+                  c.dband_of, c.dclaim, c.dbnode, c.dbcnt, c.dent_m, c.dent_w, c.dbrho, c.dbJ0,
+                  c.dA0, c.dA1, c.dCm, c.dbodies};
+  IBM_CK(h, cudaStreamSynchronize(c.stream));
+  // clear the node -> band map of the old band before its arrays go away
+  if (c.dbnode && c.dnode2band) {
+    IBM_CK(h, cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)c.geom.nx * c.geom.ny, c.stream));
+    IBM_CK(h, cudaMemsetAsync(c.dctr, 0, 2 * sizeof(int), c.stream));
+    IBM_CK(h, cudaStreamSynchronize(c.stream));
+  }
+  for (void* p : olds) dev_free(c, p);
+  c.mcap = M;
+  c.bcap = M * kStencil;
+  const size_t R = c.r_bytes;
+  IBM_ALLOC(h, c.dX, double*, M);
+  IBM_ALLOC(h, c.dY, double*, M);
+  IBM_ALLOC(h, c.dds, double*, M);
+  IBM_ALLOC(h, c.ddX, double*, M);
+  IBM_ALLOC(h, c.ddY, double*, M);
+  IBM_ALLOC(h, c.dmbody, int*, M);
+  c.dUx = dev_alloc(c, R * M);
+  c.dUy = dev_alloc(c, R * M);
+  c.dW = dev_alloc(c, R * M * kStencil);
+  IBM_ALLOC(h, c.dnode_of, int*, M * kStencil);
+  IBM_ALLOC(h, c.dband_of, int*, M * kStencil);
+  IBM_ALLOC(h, c.dclaim, int*, M * kStencil);
+  IBM_ALLOC(h, c.dbnode, int*, c.bcap);
+  IBM_ALLOC(h, c.dbcnt, int*, c.bcap);
+  IBM_ALLOC(h, c.dent_m, int*, (size_t)c.bcap * kBandCap);
+  c.dent_w = dev_alloc(c, R * (size_t)c.bcap * kBandCap);
+  c.dbrho = dev_alloc(c, R * c.bcap);
+  c.dbJ0 = dev_alloc(c, R * 2 * c.bcap);
+  c.dA0 = dev_alloc(c, R * 2 * M);
+  c.dA1 = dev_alloc(c, R * 2 * M);
+  c.dCm = dev_alloc(c, R * 3 * M);
+  IBM_ALLOC(h, c.dbodies, BodyDev*, c.nb);
+  if (!c.dUx || !c.dUy || !c.dW || !c.dent_w || !c.dbrho || !c.dbJ0 || !c.dA0 || !c.dA1 || !c.dCm)
+    return fail(h, IBM_ERR_NOMEM, "device allocation of marker arrays failed");
+  IBM_CK(h, cudaMemcpyAsync(c.dX, c.hX.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.dY, c.hY.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.dds, c.hds.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.ddX, c.hdX.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.ddY, c.hdY.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.dmbody, c.hmbody.data(), 4 * M, cudaMemcpyHostToDevice, c.stream));
+  std::vector<char> ux(R * M), uy(R * M);
+  for (int l = 0; l < M; ++l) {
+    if (R == 8) { ((double*)ux.data())[l] = c.hUx[l]; ((double*)uy.data())[l] = c.hUy[l]; }
+    else { ((float*)ux.data())[l] = (float)c.hUx[l]; ((float*)uy.data())[l] = (float)c.hUy[l]; }
+  }
+  IBM_CK(h, cudaMemcpyAsync(c.dUx, ux.data(), R * M, cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.dUy, uy.data(), R * M, cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.dbodies, c.hbodies.data(), sizeof(BodyDev) * c.nb,
+                            cudaMemcpyHostToDevice, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dA0, 0, R * 2 * M, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dA1, 0, R * 2 * M, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dCm, 0, R * 3 * M, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dbcnt, 0, sizeof(int) * c.bcap, c.stream));
+  IBM_CK(h, cudaStreamSynchronize(c.stream));   // host vectors are temporaries
+  c.band_valid = false;
+  destroy_graphs(c);
+  return IBM_OK;
+}
+
+// Device -> host copy of the moving state before markers are re-uploaded.
+ibm_status download_moving_state(Ctx* h) {
+  Ctx& c = *h;
+  if (c.nm == 0 || !c.any_moving) return IBM_OK;
+  std::vector<char> ux(c.r_bytes * c.nm), uy(c.r_bytes * c.nm);
+  IBM_CK(h, cudaMemcpyAsync(c.hX.data(), c.dX, 8 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.hY.data(), c.dY, 8 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(ux.data(), c.dUx, c.r_bytes * c.nm, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(uy.data(), c.dUy, c.r_bytes * c.nm, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.hbodies.data(), c.dbodies, sizeof(BodyDev) * c.nb, cudaMemcpyDeviceToHost,
+                            c.stream));
+  IBM_CK(h, cudaStreamSynchronize(c.stream));
+  for (int l = 0; l < c.nm; ++l) {
+    c.hUx[l] = c.r_bytes == 8 ? ((double*)ux.data())[l] : ((float*)ux.data())[l];
+    c.hUy[l] = c.r_bytes == 8 ? ((double*)uy.data())[l] : ((float*)uy.data())[l];
+  }
+  return IBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ibm_abi_version(void) { return IBM_ABI_VERSION; }
+
+ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(nullptr, IBM_ERR_INVALID, "ibm_set_allocator: give both functions or neither");
+  g_alloc = alloc;
+  g_free = release;
+  g_actx = ctx;
+  return IBM_OK;
+}
+
+const char* ibm_last_error(ibm_handle h) { return h ? h->err.c_str() : t_err.c_str(); }
+
+ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
+  if (!out) return fail(nullptr, IBM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(nullptr, IBM_ERR_INVALID, "desc is NULL");
+  const ibm_lattice_desc& d = *desc;
+  if (d.nx < 4 || d.ny < 4) return fail(nullptr, IBM_ERR_INVALID, "nx and ny must be >= 4");
+  if ((long long)d.nx * d.ny >= (1LL << 31) || d.ny > 65535)
+    return fail(nullptr, IBM_ERR_INVALID, "lattice too large (nx*ny < 2^31, ny <= 65535)");
+  if (!is_finite(d.tau) || d.tau <= 0.5) return fail(nullptr, IBM_ERR_INVALID, "tau must be finite and > 0.5");
+  if (!is_finite(d.rho0) || d.rho0 <= 0.0) return fail(nullptr, IBM_ERR_INVALID, "rho0 must be finite and > 0");
+  if (d.prec < 0 || d.prec > 3) return fail(nullptr, IBM_ERR_INVALID, "unknown precision");
+  for (int s = 0; s < 4; ++s) {
+    if (d.bc[s] < 0 || d.bc[s] > 4) return fail(nullptr, IBM_ERR_INVALID, "unknown boundary rule");
+    if (!is_finite(d.wall_u[s][0]) || !is_finite(d.wall_u[s][1]))
+      return fail(nullptr, IBM_ERR_INVALID, "wall velocity not finite");
+  }
+  if ((d.bc[0] == IBM_BC_PERIODIC) != (d.bc[1] == IBM_BC_PERIODIC) ||
+      (d.bc[2] == IBM_BC_PERIODIC) != (d.bc[3] == IBM_BC_PERIODIC))
+    return fail(nullptr, IBM_ERR_INVALID, "periodic sides must be paired");
+  if (d.bc[1] == IBM_BC_INLET_EQ || d.bc[2] == IBM_BC_INLET_EQ || d.bc[3] == IBM_BC_INLET_EQ)
+    return fail(nullptr, IBM_ERR_INVALID, "inlet supported on the -x side only");
+  if (d.bc[0] == IBM_BC_OUTLET_ZEROGRAD || d.bc[2] == IBM_BC_OUTLET_ZEROGRAD ||
+      d.bc[3] == IBM_BC_OUTLET_ZEROGRAD)
+    return fail(nullptr, IBM_ERR_INVALID, "outlet supported on the +x side only");
+  if (!is_finite(d.inlet_u[0]) || !is_finite(d.inlet_u[1]))
+    return fail(nullptr, IBM_ERR_INVALID, "inlet velocity not finite");
+  if (d.n_corr < 0 || d.n_corr > 1000) return fail(nullptr, IBM_ERR_INVALID, "n_corr must be in [0, 1000]");
+  if (!is_finite(d.corr_tol) || d.corr_tol < 0) return fail(nullptr, IBM_ERR_INVALID, "corr_tol must be >= 0");
+  if (d.delta_points != 4 && d.delta_points != 0)
+    return fail(nullptr, IBM_ERR_INVALID, "only the 4-point delta function (Eq. 15c) is built");
+
+  ibm_ctx* h = nullptr;
+  try {
+    h = new ibm_ctx();
+  } catch (...) {
+    return fail(nullptr, IBM_ERR_NOMEM, "host allocation failed");
+  }
+  DeviceGuard guard(d.device);
+  if (!guard.ok) { delete h; return fail(nullptr, IBM_ERR_CUDA, "cannot select the CUDA device"); }
+  Ctx& c = *h;
+  c.desc = d;
+  c.desc.delta_points = 4;
+  c.device = d.device;
+  c.prec = d.prec;
+  c.s_bytes = d.prec == IBM_FP64 ? 8 : (d.prec == IBM_FP32 ? 4 : 2);
+  c.r_bytes = d.prec == IBM_FP64 ? 8 : 4;
+  c.geom.nx = d.nx;
+  c.geom.ny = d.ny;
+  c.geom.nxp = (d.nx + 31) / 32 * 32;
+  c.geom.plane = (long long)d.ny * c.geom.nxp;
+  for (int s = 0; s < 4; ++s) c.geom.bc[s] = d.bc[s];
+  auto bail = [&](ibm_status st) {
+    t_err = c.err;
+    ibm_destroy(h);
+    return st;
+  };
+  if (d.cuda_stream) {
+    c.stream = (cudaStream_t)d.cuda_stream;
+  } else {
+    if (cudaStreamCreate(&c.stream) != cudaSuccess) {
+      cudaGetLastError();
+      c.err = "cudaStreamCreate failed";
+      c.stream = nullptr;
+      return bail(IBM_ERR_CUDA);
+    }
+    c.own_stream = true;
+  }
+  ibm_status st = IBM_OK;
+  do {
+    c.f = dev_alloc(c, c.s_bytes * 9 * (size_t)c.geom.plane);
+    c.macro = dev_alloc(c, c.r_bytes * 3 * (size_t)d.nx * d.ny);
+    c.dnode2band = (int*)dev_alloc(c, sizeof(int) * (size_t)d.nx * d.ny);
+    c.dctr = (int*)dev_alloc(c, 2 * sizeof(int));
+    c.dresid = dev_alloc(c, c.r_bytes * (d.n_corr + 1));
+    if (!c.f || !c.macro || !c.dnode2band || !c.dctr || !c.dresid) {
+      c.err = "device allocation of the lattice failed";
+      st = IBM_ERR_NOMEM;
+      break;
+    }
+    if (cudaMemsetAsync(c.f, 0, c.s_bytes * 9 * (size_t)c.geom.plane, c.stream) != cudaSuccess ||
+        cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)d.nx * d.ny, c.stream) != cudaSuccess ||
+        cudaMemsetAsync(c.dctr, 0, 2 * sizeof(int), c.stream) != cudaSuccess ||
+        cudaMemsetAsync(c.dresid, 0, c.r_bytes * (d.n_corr + 1), c.stream) != cudaSuccess) {
+      c.err = std::string("device memset failed: ") + cudaGetErrorString(cudaGetLastError());
+      st = IBM_ERR_CUDA;
+      break;
+    }
+    launch_fields(c, FIELD_OP_REST, nullptr, nullptr, c.stream);
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      c.err = std::string("initialisation failed: ") + cudaGetErrorString(e);
+      st = IBM_ERR_CUDA;
+      break;
+    }
+  } while (0);
+  if (st != IBM_OK) return bail(st);
+  *out = h;
+  return IBM_OK;
+}
+
+ibm_status ibm_add_markers(ibm_handle h, const double* xy, const double* ds, int n,
+                           const ibm_body_desc* body, int* body_id_out) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (!xy || n <= 0 || !body) return fail(h, IBM_ERR_INVALID, "xy, n > 0 and body are required");
+  try {
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(h, IBM_ERR_CUDA, "cannot select the CUDA device");
+    Ctx& c = *h;
+    const ibm_body_desc& b = *body;
+    if (b.kind < 0 || b.kind > 2) return fail(h, IBM_ERR_INVALID, "unknown body kind");
+    const double vals[] = {b.xc[0], b.xc[1], b.u[0], b.u[1], b.omega, b.theta, b.rho_s, b.rho_f,
+                           b.volume, b.inertia, b.radius, b.gravity[0], b.gravity[1]};
+    for (double v : vals)
+      if (!is_finite(v)) return fail(h, IBM_ERR_INVALID, "body description has a non-finite value");
+    if (b.kind == IBM_BODY_FREE &&
+        (b.rho_s <= 0 || b.rho_f <= 0 || b.volume <= 0 || b.inertia <= 0 || b.radius <= 0))
+      return fail(h, IBM_ERR_INVALID, "a free body needs rho_s, rho_f, volume, inertia, radius > 0");
+    std::vector<double> mds(n);
+    for (int k = 0; k < n; ++k)
+      if (!is_finite(xy[2 * k]) || !is_finite(xy[2 * k + 1]))
+        return fail(h, IBM_ERR_INVALID, "marker position not finite");
+    if (ds) {
+      for (int k = 0; k < n; ++k) {
+        if (!is_finite(ds[k]) || ds[k] <= 0) return fail(h, IBM_ERR_INVALID, "ds must be finite and > 0");
+        mds[k] = ds[k];
+      }
+    } else {
+      double per = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const int k2 = (k + 1) % n;
+        per += std::hypot(xy[2 * k2] - xy[2 * k], xy[2 * k2 + 1] - xy[2 * k + 1]);
+      }
+      if (!(per > 0)) return fail(h, IBM_ERR_INVALID, "cannot derive ds from a zero perimeter");
+      for (int k = 0; k < n; ++k) mds[k] = per / n;
+    }
+    // The 4 x 4 support of every marker must stay inside closed axes and off
+    // the inlet / outlet columns.
+    const Geom& g = c.geom;
+    for (int k = 0; k < n; ++k) {
+      const long long bx = (long long)std::floor(xy[2 * k]) - 1, by = (long long)std::floor(xy[2 * k + 1]) - 1;
+      if (g.bc[0] != BC_PERIODIC) {
+        const long long lo = g.bc[0] == BC_INLET ? 1 : 0;
+        const long long hi = g.bc[1] == BC_OUTLET ? g.nx - 3 : g.nx - 1;
+        if (bx < lo || bx + 3 > hi)
+          return fail(h, IBM_ERR_INVALID, "a marker support leaves the domain or touches an inlet/outlet column");
+      }
+      if (g.bc[2] != BC_PERIODIC && (by < 0 || by + 3 > g.ny - 1))
+        return fail(h, IBM_ERR_INVALID, "a marker support leaves the domain in y");
+    }
+    {
+      ibm_status st = download_moving_state(h);
+      if (st != IBM_OK) return st;
+    }
+    BodyDev B{};
+    B.kind = b.kind;
+    B.m0 = c.nm;
+    B.m1 = c.nm + n;
+    B.xc[0] = b.xc[0]; B.xc[1] = b.xc[1];
+    B.u[0] = b.u[0]; B.u[1] = b.u[1];
+    B.omega = b.omega; B.theta = b.theta;
+    B.u_prev[0] = b.u[0]; B.u_prev[1] = b.u[1];
+    B.omega_prev = b.omega; B.theta0 = b.theta;
+    B.rho_s = b.rho_s; B.rho_f = b.rho_f; B.volume = b.volume; B.inertia = b.inertia;
+    B.radius = b.radius; B.mass = b.rho_s * b.volume;
+    B.gravity[0] = b.gravity[0]; B.gravity[1] = b.gravity[1];
+    for (int k = 0; k < n; ++k) {
+      const double X = xy[2 * k], Y = xy[2 * k + 1];
+      c.hX.push_back(X);
+      c.hY.push_back(Y);
+      c.hds.push_back(mds[k]);
+      c.hdX.push_back(X - b.xc[0]);
+      c.hdY.push_back(Y - b.xc[1]);
+      c.hUx.push_back(b.u[0] - b.omega * (Y - b.xc[1]));
+      c.hUy.push_back(b.u[1] + b.omega * (X - b.xc[0]));
+      c.hmbody.push_back(c.nb);
+    }
+    c.hbodies.push_back(B);
+    c.nm += n;
+    const int id = c.nb++;
+    if (b.kind != IBM_BODY_FIXED) c.any_moving = true;
+    ibm_status st = upload_markers(h);
+    if (st != IBM_OK) return st;
+    if (body_id_out) *body_id_out = id;
+    return IBM_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(h, IBM_ERR_NOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(h, IBM_ERR_INVALID, "unexpected error in ibm_add_markers");
+  }
+}
+
+ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (nsteps < 0) return fail(h, IBM_ERR_INVALID, "nsteps must be >= 0");
+  if (nsteps == 0) return IBM_OK;
+  try {
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(h, IBM_ERR_CUDA, "cannot select the CUDA device");
+    Ctx& c = *h;
+    const bool timing = (flags & IBM_STEP_TIME_KERNELS) != 0;
+    const bool use_graph = !(flags & (IBM_STEP_NO_GRAPH | IBM_STEP_TIME_KERNELS));
+    if (timing && c.ev.empty()) {
+      c.ev.resize(2 * kEventPairs);
+      for (auto& e : c.ev) IBM_CK(h, cudaEventCreate(&e));
+    }
+    if (c.nm > 0 && !c.band_valid) {
+      launch_band_build(c, c.stream);
+      c.band_valid = true;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+      const int parity = c.parity;
+      const int macro = (k == nsteps - 1 && !(flags & IBM_STEP_NO_MACRO)) ? 1 : 0;
+      if (use_graph) {
+        if (!c.graph[parity][macro]) {
+          cudaGraph_t graph;
+          IBM_CK(h, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+          enqueue_step(c, parity, macro != 0, false);
+          IBM_CK(h, cudaStreamEndCapture(c.stream, &graph));
+          cudaError_t e = cudaGraphInstantiate(&c.graph[parity][macro], graph, 0);
+          cudaGraphDestroy(graph);
+          if (e != cudaSuccess) {
+            c.graph[parity][macro] = nullptr;
+            cudaGetLastError();
+            return fail(h, IBM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+          }
+        }
+        IBM_CK(h, cudaGraphLaunch(c.graph[parity][macro], c.stream));
+      } else {
+        if (timing && c.ev_used >= kEventPairs) {
+          ibm_status st = fold_events(h);
+          if (st != IBM_OK) return st;
+        }
+        enqueue_step(c, parity, macro != 0, timing);
+        IBM_CK(h, cudaGetLastError());
+      }
+      c.parity ^= 1;
+      c.launches += kernels_per_step(c);
+      c.steps += 1;
+    }
+    IBM_CK(h, cudaGetLastError());
+    return IBM_OK;
+  } catch (...) {
+    return fail(h, IBM_ERR_INVALID, "unexpected error in ibm_step");
+  }
+}
+
+ibm_status ibm_sync(ibm_handle h) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  DeviceGuard guard(h->device);
+  return sync_stream(h);
+}
+
+ibm_status ibm_read_fields(ibm_handle h, int field, double* host_dst, size_t n_elems) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (!host_dst) return fail(h, IBM_ERR_INVALID, "host_dst is NULL");
+  try {
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(h, IBM_ERR_CUDA, "cannot select the CUDA device");
+    Ctx& c = *h;
+    const size_t n = (size_t)c.geom.nx * c.geom.ny;
+    ibm_status st = sync_stream(h);
+    if (st != IBM_OK) return st;
+    switch (field) {
+      case IBM_FIELD_RHO:
+      case IBM_FIELD_UX:
+      case IBM_FIELD_UY: {
+        if (n_elems != n) return fail(h, IBM_ERR_INVALID, "n_elems must be nx*ny");
+        if ((st = ensure_io(h, 3 * n)) != IBM_OK) return st;
+        launch_fields(c, FIELD_OP_MACRO_OUT, nullptr, c.dio, c.stream);
+        const size_t off = (size_t)(field - IBM_FIELD_RHO) * n;
+        IBM_CK(h, cudaMemcpyAsync(host_dst, c.dio + off, 8 * n, cudaMemcpyDeviceToHost, c.stream));
+        break;
+      }
+      case IBM_FIELD_F: {
+        if (n_elems != 9 * n) return fail(h, IBM_ERR_INVALID, "n_elems must be 9*nx*ny");
+        if ((st = ensure_io(h, 9 * n)) != IBM_OK) return st;
+        launch_fields(c, FIELD_OP_READ_F, nullptr, c.dio, c.stream);
+        IBM_CK(h, cudaMemcpyAsync(host_dst, c.dio, 8 * 9 * n, cudaMemcpyDeviceToHost, c.stream));
+        break;
+      }
+      case IBM_FIELD_BODIES: {
+        if (n_elems != (size_t)9 * c.nb) return fail(h, IBM_ERR_INVALID, "n_elems must be 9*nbodies");
+        std::vector<BodyDev> bd(c.nb);
+        if (c.nb)
+          IBM_CK(h, cudaMemcpyAsync(bd.data(), c.dbodies, sizeof(BodyDev) * c.nb, cudaMemcpyDeviceToHost,
+                                    c.stream));
+        IBM_CK(h, cudaStreamSynchronize(c.stream));
+        for (int b = 0; b < c.nb; ++b) {
+          double* o = host_dst + 9 * b;
+          o[0] = bd[b].xc[0]; o[1] = bd[b].xc[1]; o[2] = bd[b].u[0]; o[3] = bd[b].u[1];
+          o[4] = bd[b].omega; o[5] = bd[b].theta; o[6] = bd[b].F_ib[0]; o[7] = bd[b].F_ib[1];
+          o[8] = bd[b].T_ib;
+        }
+        return IBM_OK;
+      }
+      case IBM_FIELD_RESIDUAL: {
+        const int N = c.desc.n_corr;
+        if (n_elems != (size_t)N + 1) return fail(h, IBM_ERR_INVALID, "n_elems must be n_corr+1");
+        std::vector<char> raw(c.r_bytes * (N + 1));
+        IBM_CK(h, cudaMemcpyAsync(raw.data(), c.dresid, raw.size(), cudaMemcpyDeviceToHost, c.stream));
+        IBM_CK(h, cudaStreamSynchronize(c.stream));
+        for (int k = 0; k <= N; ++k)
+          host_dst[k] = c.r_bytes == 8 ? ((double*)raw.data())[k] : (double)((float*)raw.data())[k];
+        if (c.desc.corr_tol > 0 && !(host_dst[N] <= c.desc.corr_tol))
+          return fail(h, IBM_WARN_NOT_CONVERGED, "no-slip residual above corr_tol after n_corr iterations");
+        return IBM_OK;
+      }
+      case IBM_FIELD_MARKERS: {
+        if (n_elems != (size_t)2 * c.nm) return fail(h, IBM_ERR_INVALID, "n_elems must be 2*nmarkers");
+        std::vector<double> X(c.nm), Y(c.nm);
+        if (c.nm) {
+          IBM_CK(h, cudaMemcpyAsync(X.data(), c.dX, 8 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+          IBM_CK(h, cudaMemcpyAsync(Y.data(), c.dY, 8 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+        }
+        IBM_CK(h, cudaStreamSynchronize(c.stream));
+        for (int l = 0; l < c.nm; ++l) { host_dst[2 * l] = X[l]; host_dst[2 * l + 1] = Y[l]; }
+        return IBM_OK;
+      }
+      default:
+        return fail(h, IBM_ERR_INVALID, "unknown field");
+    }
+    IBM_CK(h, cudaStreamSynchronize(c.stream));
+    IBM_CK(h, cudaGetLastError());
+    return IBM_OK;
+  } catch (...) {
+    return fail(h, IBM_ERR_INVALID, "unexpected error in ibm_read_fields");
+  }
+}
+
+ibm_status ibm_write_fields(ibm_handle h, int field, const double* host_src, size_t n_elems) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (!host_src) return fail(h, IBM_ERR_INVALID, "host_src is NULL");
+  try {
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(h, IBM_ERR_CUDA, "cannot select the CUDA device");
+    Ctx& c = *h;
+    const size_t n = (size_t)c.geom.nx * c.geom.ny;
+    ibm_status st = IBM_OK;
+    if (field == IBM_FIELD_F) {
+      if (n_elems != 9 * n) return fail(h, IBM_ERR_INVALID, "n_elems must be 9*nx*ny");
+      for (size_t k = 0; k < 9 * n; ++k)
+        if (!is_finite(host_src[k])) return fail(h, IBM_ERR_INVALID, "populations must be finite");
+      if ((st = ensure_io(h, 9 * n)) != IBM_OK) return st;
+      IBM_CK(h, cudaMemcpyAsync(c.dio, host_src, 8 * 9 * n, cudaMemcpyHostToDevice, c.stream));
+      launch_fields(c, FIELD_OP_WRITE_F, c.dio, nullptr, c.stream);
+      c.parity = 0;
+      launch_fields(c, FIELD_OP_MACROS, nullptr, nullptr, c.stream);
+    } else if (field == IBM_FIELD_MACRO_INIT) {
+      if (n_elems != 3 * n) return fail(h, IBM_ERR_INVALID, "n_elems must be 3*nx*ny");
+      for (size_t k = 0; k < 3 * n; ++k)
+        if (!is_finite(host_src[k])) return fail(h, IBM_ERR_INVALID, "fields must be finite");
+      for (size_t k = 0; k < n; ++k)
+        if (!(host_src[k] > 0)) return fail(h, IBM_ERR_INVALID, "density must be > 0");
+      if ((st = ensure_io(h, 3 * n)) != IBM_OK) return st;
+      IBM_CK(h, cudaMemcpyAsync(c.dio, host_src, 8 * 3 * n, cudaMemcpyHostToDevice, c.stream));
+      launch_fields(c, FIELD_OP_INIT_EQ, c.dio, nullptr, c.stream);
+      c.parity = 0;
+    } else {
+      return fail(h, IBM_ERR_INVALID, "field is not writable");
+    }
+    return sync_stream(h);
+  } catch (...) {
+    return fail(h, IBM_ERR_INVALID, "unexpected error in ibm_write_fields");
+  }
+}
+
+ibm_status ibm_kernel_times(ibm_handle h, double* ms_total, int* launches) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  DeviceGuard guard(h->device);
+  ibm_status st = fold_events(h);
+  if (st != IBM_OK) return st;
+  if (ms_total) *ms_total = h->acc_ms;
+  if (launches) *launches = h->acc_n;
+  h->acc_ms = 0.0;
+  h->acc_n = 0;
+  return IBM_OK;
+}
+
+ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodies, int* band_nodes) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  DeviceGuard guard(h->device);
+  if (nodes) *nodes = (long long)h->geom.nx * h->geom.ny;
+  if (markers) *markers = h->nm;
+  if (bodies) *bodies = h->nb;
+  if (band_nodes) {
+    int ctr[2] = {0, 0};
+    if (h->nm > 0 && !h->band_valid) {
+      launch_band_build(*h, h->stream);
+      h->band_valid = true;
+    }
+    IBM_CK(h, cudaMemcpyAsync(ctr, h->dctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
+    IBM_CK(h, cudaStreamSynchronize(h->stream));
+    *band_nodes = h->nm > 0 ? ctr[0] : 0;
+  }
+  return IBM_OK;
+}
+
+ibm_status ibm_get_counters(ibm_handle h, long long* kernel_launches, long long* steps) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (kernel_launches) *kernel_launches = h->launches;
+  if (steps) *steps = h->steps;
+  return IBM_OK;
+}
+
+ibm_status ibm_destroy(ibm_handle h) {
+  if (!h) return IBM_OK;
+  ibm_status st = IBM_OK;
+  {
+    DeviceGuard guard(h->device);
+    if (h->stream && cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      st = IBM_ERR_CUDA;
+    }
+    destroy_graphs(*h);
+    for (auto& e : h->ev) cudaEventDestroy(e);
+    std::vector<void*> all = h->allocs;
+    for (void* p : all) dev_free(*h, p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  }
+  delete h;
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,483 @@
+// ibm_ib.cu -- the immersed-boundary side of a step (arXiv 1803.09380,
+// section 2.3): the distribution-function correction loop, body force and
+// torque, and the rigid-body update.
+//
+// Moment form of the correction.  The nodal equilibrium of Eq. 3 is linear in
+// (rho, j = rho u, Pi = rho u u):  f_i^eq = w_i [rho + 3 e.j + 9/2 ee:Pi -
+// 3/2 tr Pi].  So the interpolated equilibria of Eq. 28 are the equilibria of
+// the interpolated moments (rho*, j*, Pi*), and with the boundary density
+// rho_b = rho* the deviation of Eq. 28 is
+//     delta f_i = w_i [3 e.dj + 9/2 ee:dPi - 3/2 tr dPi],
+//     dj = rho* U - j*,   dPi = rho* U U - Pi*.
+// Spreading (Eq. 26) and correction (Eq. 27) are linear too: node x gains
+// momentum sum_l W_l(x) ds_l dj_l and keeps its density, while the spread dPi
+// changes only the second moment of f, which no later interpolation reads
+// (interpolation uses the nodal equilibrium, i.e. rho and j).  Hence the N
+// iterations run entirely on small per-band-node and per-marker arrays:
+//     j^n(x) = j^0(x) + sum_{l covers x} W_l(x) ds_l A^n_l,   A^n_l = sum_{k<n} dj^k_l,
+// and f is touched twice per step: a gather of (rho, j^0) on the band nodes
+// and one final application of the summed correction.  The same identity
+// gives the force of Eq. 29: F_body = -sum_l ds_l A^N_l.
+//
+// Determinism: each band node sums its covering markers in ascending marker
+// order (lists sorted after the parallel build), and every reduction has a
+// fixed tree shape; no floating-point atomics.
+#include "ibm_internal.h"
+
+namespace ibm {
+
+// Eq. 15c in double precision: 1/4 (1 + cos(pi |r| / 2)), zero for |r| >= 2.
+__device__ __forceinline__ double delta4(double r) {
+  const double a = fabs(r);
+  return a >= 2.0 ? 0.0 : 0.25 * (1.0 + cospi(0.5 * a));
+}
+
+__device__ __forceinline__ int wrap_axis(int c, int n, bool periodic) {
+  if (periodic) { c %= n; return c < 0 ? c + n : c; }
+  return (c < 0 || c >= n) ? -1 : c;
+}
+
+// Maximum that keeps a NaN (a diverged residual must not be hidden).
+template <class R>
+__device__ __forceinline__ R nanmax(R a, R b) { return (a > b || a != a) ? a : b; }
+
+template <class R> struct AtomicBits;
+template <> struct AtomicBits<float> {
+  static __device__ void max(float* a, float v) { atomicMax((unsigned int*)a, __float_as_uint(v)); }
+};
+template <> struct AtomicBits<double> {
+  static __device__ void max(double* a, double v) {
+    atomicMax((unsigned long long*)a, (unsigned long long)__double_as_longlong(v));
+  }
+};
+
+// ------------------------------------------------------------------ band build
+// One thread per (marker, stencil slot).  Clearing the previous band, then
+// claim / allocate / fill / sort in separate launches (kernel boundaries are
+// the only ordering used, so no thread ever waits on another).
+__global__ void k_band_clear(const int* __restrict__ ctr, const int* __restrict__ bnode,
+                             int* __restrict__ node2band, int bcap) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb = min(ctr[0], bcap);
+  if (b < nb) node2band[bnode[b]] = -1;
+}
+
+template <class R>
+__global__ void k_band_claim(Geom g, int M, const double* __restrict__ X, const double* __restrict__ Y,
+                             R* __restrict__ W, int* __restrict__ node_of, int* __restrict__ node2band,
+                             int* __restrict__ claim) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * kStencil) return;
+  const int l = t / kStencil, s = t % kStencil;
+  const double Xl = X[l], Yl = Y[l];
+  const int bx = (int)floor(Xl) - 1 + (s & 3), by = (int)floor(Yl) - 1 + (s >> 2);
+  const int x = wrap_axis(bx, g.nx, g.bc[0] == BC_PERIODIC);
+  const int y = wrap_axis(by, g.ny, g.bc[2] == BC_PERIODIC);
+  int n = -1;
+  double w = 0.0;
+  if (x >= 0 && y >= 0) {
+    n = y * g.nx + x;
+    w = delta4(Xl - (double)bx) * delta4(Yl - (double)by);
+  }
+  W[t] = (R)w;
+  node_of[t] = n;
+  claim[t] = (n >= 0) ? (atomicCAS(&node2band[n], -1, -2) == -1) : 0;
+}
+
+__global__ void k_band_alloc(int M, const int* __restrict__ node_of, const int* __restrict__ claim,
+                             int* __restrict__ node2band, int* __restrict__ bnode,
+                             int* __restrict__ bcnt, int* __restrict__ ctr, int bcap) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * kStencil || !claim[t]) return;
+  const int n = node_of[t];
+  const int b = atomicAdd(&ctr[0], 1);
+  if (b < bcap) {
+    bnode[b] = n;
+    bcnt[b] = 0;
+    node2band[n] = b;
+  } else {
+    atomicOr(&ctr[1], ERR_BAND_CAP);
+  }
+}
+
+template <class R>
+__global__ void k_band_fill(int M, const int* __restrict__ node_of, const R* __restrict__ W,
+                            const double* __restrict__ ds, const int* __restrict__ node2band,
+                            int* __restrict__ band_of, int* __restrict__ bcnt,
+                            int* __restrict__ ent_m, R* __restrict__ ent_w, int* __restrict__ ctr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * kStencil) return;
+  const int n = node_of[t];
+  const int b = n >= 0 ? node2band[n] : -1;
+  band_of[t] = b;
+  if (b < 0) return;
+  const int l = t / kStencil;
+  const int pos = atomicAdd(&bcnt[b], 1);
+  if (pos < kBandCap) {
+    ent_m[(long long)b * kBandCap + pos] = l;
+    ent_w[(long long)b * kBandCap + pos] = (R)((double)W[t] * ds[l]);
+  } else {
+    atomicOr(&ctr[1], ERR_LIST_CAP);
+  }
+}
+
+template <class R>
+__global__ void k_band_sort(const int* __restrict__ ctr, int* __restrict__ bcnt,
+                            int* __restrict__ ent_m, R* __restrict__ ent_w, int bcap) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= min(ctr[0], bcap)) return;
+  const int n = min(bcnt[b], kBandCap);
+  bcnt[b] = n;
+  int* m = ent_m + (long long)b * kBandCap;
+  R* w = ent_w + (long long)b * kBandCap;
+  for (int i = 1; i < n; ++i) {          // insertion sort by marker id
+    const int km = m[i];
+    const R kw = w[i];
+    int j = i - 1;
+    while (j >= 0 && m[j] > km) { m[j + 1] = m[j]; w[j + 1] = w[j]; --j; }
+    m[j + 1] = km; w[j + 1] = kw;
+  }
+}
+
+// ------------------------------------------------------------------ IB loop
+// Gather (rho, j^0) at every band node from the post-stream populations.
+template <int P>
+__global__ void k_ib_gather(Geom g, StepConsts<typename Prec<P>::R> c,
+                            const typename Prec<P>::S* __restrict__ A, int parity,
+                            const int* __restrict__ ctr, const int* __restrict__ bnode,
+                            typename Prec<P>::R* __restrict__ brho, typename Prec<P>::R* __restrict__ bJ,
+                            int bcap) {
+  typedef typename Prec<P>::R R;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= min(ctr[0], bcap)) return;
+  const int n = bnode[b];
+  const int x = n % g.nx, y = n / g.nx;
+  R p[9], rho, jx, jy;
+  long long where;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) p[i] = post_stream<P>(g, c, A, parity, x, y, i, where);
+  moments9<R>(p, rho, jx, jy);
+  brho[b] = rho;
+  bJ[2 * b] = jx;
+  bJ[2 * b + 1] = jy;
+}
+
+// Current momentum of band node b: j^0 plus the spread of the accumulated
+// deviations A of the markers covering it, in ascending marker order.
+template <class R>
+__device__ __forceinline__ void band_momentum(int b, const R* __restrict__ bJ, const int* __restrict__ bcnt,
+                                              const int* __restrict__ ent_m, const R* __restrict__ ent_w,
+                                              const R* __restrict__ Acc, R& jx, R& jy) {
+  jx = bJ[2 * b];
+  jy = bJ[2 * b + 1];
+  const int n = bcnt[b];
+  const long long o = (long long)b * kBandCap;
+  for (int e = 0; e < n; ++e) {
+    const int m = ent_m[o + e];
+    const R w = ent_w[o + e];
+    jx += w * Acc[2 * m];
+    jy += w * Acc[2 * m + 1];
+  }
+}
+
+// One correction iteration (or, with UPDATE = false, the residual pass):
+// 16 lanes per marker, one per stencil node.  Each lane forms its node's
+// current rho, j, Pi = j j / rho, weighted by W; a 16-lane butterfly gives
+// (rho*, j*, Pi*) (Eq. 22b with Eq. 28 in moment form); lane 0 forms the
+// deviation, accumulates A and C, and the residual |j*/rho* - U|.
+template <class R, bool FIRST, bool UPDATE>
+__global__ void __launch_bounds__(256) k_ib_iterate(
+    int M, const int* __restrict__ band_of, const R* __restrict__ W, const R* __restrict__ brho,
+    const R* __restrict__ bJ, const int* __restrict__ bcnt, const int* __restrict__ ent_m,
+    const R* __restrict__ ent_w, const R* __restrict__ Ain, R* __restrict__ Aout, R* __restrict__ Cm,
+    const R* __restrict__ Ux, const R* __restrict__ Uy, R* __restrict__ resid) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = t / kStencil;
+  const bool valid = l < M;
+  const int b = valid ? band_of[t] : -1;
+  R w = R(0), rho = R(1), jx = R(0), jy = R(0);
+  if (b >= 0) {
+    w = W[t];
+    rho = brho[b];
+    if (FIRST) { jx = bJ[2 * b]; jy = bJ[2 * b + 1]; }
+    else band_momentum<R>(b, bJ, bcnt, ent_m, ent_w, Ain, jx, jy);
+  }
+  const R inv = R(1) / rho;
+  R v0 = w * rho, v1 = w * jx, v2 = w * jy;
+  R v3 = w * (jx * jx * inv), v4 = w * (jx * jy * inv), v5 = w * (jy * jy * inv);
+#pragma unroll
+  for (int off = kStencil / 2; off >= 1; off >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+    v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+    v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+    v4 += __shfl_xor_sync(0xffffffffu, v4, off);
+    v5 += __shfl_xor_sync(0xffffffffu, v5, off);
+  }
+  R r = R(0);
+  if (valid && (t % kStencil) == 0) {
+    const R ux = Ux[l], uy = Uy[l];
+    const R rs = v0;
+    const R ex = v1 / rs - ux, ey = v2 / rs - uy;
+    r = sqrt(ex * ex + ey * ey);
+    if (UPDATE) {
+      const R djx = rs * ux - v1, djy = rs * uy - v2;
+      const R dpxx = rs * ux * ux - v3, dpxy = rs * ux * uy - v4, dpyy = rs * uy * uy - v5;
+      if (FIRST) {
+        Aout[2 * l] = djx; Aout[2 * l + 1] = djy;
+        Cm[3 * l] = dpxx; Cm[3 * l + 1] = dpxy; Cm[3 * l + 2] = dpyy;
+      } else {
+        Aout[2 * l] = Ain[2 * l] + djx; Aout[2 * l + 1] = Ain[2 * l + 1] + djy;
+        Cm[3 * l] += dpxx; Cm[3 * l + 1] += dpxy; Cm[3 * l + 2] += dpyy;
+      }
+    }
+  }
+  // block max of the residual, one atomic per block
+  __shared__ R red[256 / 32];
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) r = nanmax(r, __shfl_xor_sync(0xffffffffu, r, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R m = red[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = nanmax(m, red[k]);
+    if (m > R(0) || m != m) AtomicBits<R>::max(resid, m);
+  }
+}
+
+// Apply the summed correction of all iterations at every band node (Eq. 27
+// summed over n): f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi].
+template <int P>
+__global__ void k_ib_apply(Geom g, StepConsts<typename Prec<P>::R> c, typename Prec<P>::S* __restrict__ A,
+                           int parity, const int* __restrict__ ctr, const int* __restrict__ bnode,
+                           const int* __restrict__ bcnt, const int* __restrict__ ent_m,
+                           const typename Prec<P>::R* __restrict__ ent_w,
+                           const typename Prec<P>::R* __restrict__ Acc,
+                           const typename Prec<P>::R* __restrict__ Cm, int bcap) {
+  typedef typename Prec<P>::R R;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= min(ctr[0], bcap)) return;
+  R jx = R(0), jy = R(0), pxx = R(0), pxy = R(0), pyy = R(0);
+  const int cnt = bcnt[b];
+  const long long o = (long long)b * kBandCap;
+  for (int e = 0; e < cnt; ++e) {
+    const int m = ent_m[o + e];
+    const R w = ent_w[o + e];
+    jx += w * Acc[2 * m];
+    jy += w * Acc[2 * m + 1];
+    pxx += w * Cm[3 * m];
+    pxy += w * Cm[3 * m + 1];
+    pyy += w * Cm[3 * m + 2];
+  }
+  const int n = bnode[b];
+  const int x = n % g.nx, y = n / g.nx;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    long long where;
+    post_stream<P>(g, c, A, parity, x, y, i, where);
+    if (where < 0) continue;
+    const int slot = (int)(where / g.plane);
+    const R df = feq_i<R>(i, R(0), jx, jy, pxx, pxy, pyy);
+    A[where] = Prec<P>::st(Prec<P>::ld(A[where], slot) + df, slot);
+  }
+}
+
+// ------------------------------------------------------------------ bodies
+// Eq. 29 per body in FP64 with a fixed-shape block reduction:
+// F = -sum_l ds_l A_l,  T = sum_l (X_l - x_c) x F_l.
+template <class R>
+__global__ void __launch_bounds__(256) k_body_force(BodyDev* __restrict__ bodies,
+                                                   const double* __restrict__ X, const double* __restrict__ Y,
+                                                   const double* __restrict__ ds, const R* __restrict__ Acc) {
+  BodyDev& B = bodies[blockIdx.x];
+  double fx = 0.0, fy = 0.0, tq = 0.0;
+  for (int l = B.m0 + threadIdx.x; l < B.m1; l += blockDim.x) {
+    const double Fx = -ds[l] * (double)Acc[2 * l], Fy = -ds[l] * (double)Acc[2 * l + 1];
+    fx += Fx;
+    fy += Fy;
+    tq += (X[l] - B.xc[0]) * Fy - (Y[l] - B.xc[1]) * Fx;
+  }
+  __shared__ double s[3][256];
+  s[0][threadIdx.x] = fx; s[1][threadIdx.x] = fy; s[2][threadIdx.x] = tq;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { B.F_ib[0] = s[0][0]; B.F_ib[1] = s[1][0]; B.T_ib = s[2][0]; }
+}
+
+// Eq. 39 on body i from a partner at offset d = x_i - x_j.
+__device__ void collision_force(const BodyDev& Bi, double Rj, double dx, double dy, double* F) {
+  const double eps_c = 0.01, xi = 0.05 * 2.0 * Bi.radius;
+  const double gmag = sqrt(Bi.gravity[0] * Bi.gravity[0] + Bi.gravity[1] * Bi.gravity[1]);
+  const double cij = Bi.mass * (1.0 - Bi.rho_f / Bi.rho_s) * gmag;
+  const double d = sqrt(dx * dx + dy * dy);
+  if (d > Bi.radius + Rj + xi || d <= 0.0) return;
+  const double s = (d - Bi.radius - Rj - xi) / xi;
+  F[0] += cij / eps_c * s * s * dx / d;
+  F[1] += cij / eps_c * s * s * dy / d;
+}
+
+// Newton-Euler update of every body (one block, one thread per body, FP64):
+// Eqs. 37-38 (internal-mass terms, lagged), 39 (collisions with other free
+// bodies and with mirror images across closed walls), 40-42.
+__global__ void k_body_update(Geom g, BodyDev* __restrict__ bodies, int nb) {
+  const int b = threadIdx.x;
+  double Fc[2] = {0.0, 0.0};
+  BodyDev B;
+  if (b < nb) {
+    B = bodies[b];
+    if (B.kind == IBM_BODY_FREE) {
+      for (int o = 0; o < nb; ++o) {
+        if (o == b || bodies[o].kind != IBM_BODY_FREE) continue;
+        collision_force(B, bodies[o].radius, B.xc[0] - bodies[o].xc[0], B.xc[1] - bodies[o].xc[1], Fc);
+      }
+      for (int s = 0; s < 4; ++s) {
+        if (g.bc[s] != BC_BOUNCEBACK && g.bc[s] != BC_FREESLIP) continue;
+        const double w = s == 0 ? -0.5 : (s == 1 ? g.nx - 0.5 : (s == 2 ? -0.5 : g.ny - 0.5));
+        if (s < 2) collision_force(B, B.radius, B.xc[0] - (2.0 * w - B.xc[0]), 0.0, Fc);
+        else collision_force(B, B.radius, 0.0, B.xc[1] - (2.0 * w - B.xc[1]), Fc);
+      }
+    }
+  }
+  __syncthreads();   // every body read the old positions before any update
+  if (b >= nb) return;
+  if (B.kind == IBM_BODY_FREE) {
+    double Ft[2];
+    for (int d = 0; d < 2; ++d)
+      Ft[d] = B.F_ib[d] + B.rho_f * B.volume * (B.u[d] - B.u_prev[d]) + Fc[d] +
+              B.mass * (1.0 - B.rho_f / B.rho_s) * B.gravity[d];
+    const double Tt = B.T_ib + B.rho_f / B.rho_s * B.inertia * (B.omega - B.omega_prev);
+    const double un0 = B.u[0], un1 = B.u[1], wn = B.omega;
+    B.xc[0] += un0 + 0.5 * Ft[0] / B.mass;
+    B.xc[1] += un1 + 0.5 * Ft[1] / B.mass;
+    B.theta += wn + 0.5 * Tt / B.inertia;
+    B.u_prev[0] = un0; B.u_prev[1] = un1;
+    B.u[0] = un0 + Ft[0] / B.mass;
+    B.u[1] = un1 + Ft[1] / B.mass;
+    B.omega_prev = wn;
+    B.omega = wn + Tt / B.inertia;
+  } else if (B.kind == IBM_BODY_PRESCRIBED) {
+    B.xc[0] += B.u[0];
+    B.xc[1] += B.u[1];
+    B.theta += B.omega;
+  }
+  bodies[b] = B;
+}
+
+// Rigid motion of the markers of moving bodies and their new velocities
+// U + omega x (X - x_c).
+template <class R>
+__global__ void k_marker_move(int M, const BodyDev* __restrict__ bodies, const int* __restrict__ mbody,
+                              const double* __restrict__ dX, const double* __restrict__ dY,
+                              double* __restrict__ X, double* __restrict__ Y, R* __restrict__ Ux,
+                              R* __restrict__ Uy) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= M) return;
+  const BodyDev& B = bodies[mbody[l]];
+  if (B.kind == IBM_BODY_FIXED) return;
+  double sn, cs;
+  sincos(B.theta - B.theta0, &sn, &cs);
+  const double x = B.xc[0] + cs * dX[l] - sn * dY[l];
+  const double y = B.xc[1] + sn * dX[l] + cs * dY[l];
+  X[l] = x;
+  Y[l] = y;
+  Ux[l] = (R)(B.u[0] - B.omega * (y - B.xc[1]));
+  Uy[l] = (R)(B.u[1] + B.omega * (x - B.xc[0]));
+}
+
+// ------------------------------------------------------------------ launchers
+static unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <class R>
+static void band_build_t(const Ctx& h, cudaStream_t s) {
+  const int T = h.nm * kStencil;
+  if (T == 0) return;
+  k_band_clear<<<blocks_for(h.bcap, 256), 256, 0, s>>>(h.dctr, h.dbnode, h.dnode2band, h.bcap);
+  cudaMemsetAsync(h.dctr, 0, sizeof(int), s);
+  k_band_claim<R><<<blocks_for(T, 256), 256, 0, s>>>(h.geom, h.nm, h.dX, h.dY, (R*)h.dW, h.dnode_of,
+                                                      h.dnode2band, h.dclaim);
+  k_band_alloc<<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, h.dclaim, h.dnode2band, h.dbnode,
+                                                  h.dbcnt, h.dctr, h.bcap);
+  k_band_fill<R><<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, (const R*)h.dW, h.dds, h.dnode2band,
+                                                     h.dband_of, h.dbcnt, h.dent_m, (R*)h.dent_w, h.dctr);
+  k_band_sort<R><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.dctr, h.dbcnt, h.dent_m, (R*)h.dent_w, h.bcap);
+}
+
+void launch_band_build(const Ctx& h, cudaStream_t s) {
+  if (h.r_bytes == 8) band_build_t<double>(h, s);
+  else band_build_t<float>(h, s);
+}
+
+template <int P>
+static void ib_loop_t(const Ctx& h, int parity, cudaStream_t s) {
+  typedef typename Prec<P>::S S;
+  typedef typename Prec<P>::R R;
+  if (h.nm == 0) return;
+  const int N = h.desc.n_corr;
+  StepConsts<R> c = make_consts<R>(h);
+  S* A = (S*)h.f;
+  cudaMemsetAsync(h.dresid, 0, sizeof(R) * (N + 1), s);
+  k_ib_gather<P><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.geom, c, A, parity, h.dctr, h.dbnode,
+                                                         (R*)h.dbrho, (R*)h.dbJ0, h.bcap);
+  const unsigned gridM = blocks_for((long long)h.nm * kStencil, 256);
+  R* Acc[2] = {(R*)h.dA0, (R*)h.dA1};
+  R* resid = (R*)h.dresid;
+  for (int n = 0; n < N; ++n) {
+    const R* ain = Acc[n & 1];
+    R* aout = Acc[(n + 1) & 1];
+    if (n == 0)
+      k_ib_iterate<R, true, true><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
+          (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, ain, aout, (R*)h.dCm,
+          (const R*)h.dUx, (const R*)h.dUy, resid + n);
+    else
+      k_ib_iterate<R, false, true><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
+          (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, ain, aout, (R*)h.dCm,
+          (const R*)h.dUx, (const R*)h.dUy, resid + n);
+  }
+  const R* afin = Acc[N & 1];
+  if (N == 0)
+    k_ib_iterate<R, true, false><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
+        (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, afin, nullptr, nullptr,
+        (const R*)h.dUx, (const R*)h.dUy, resid + N);
+  else
+    k_ib_iterate<R, false, false><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
+        (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, afin, nullptr, nullptr,
+        (const R*)h.dUx, (const R*)h.dUy, resid + N);
+  if (N > 0) {
+    k_ib_apply<P><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.geom, c, A, parity, h.dctr, h.dbnode, h.dbcnt,
+        h.dent_m, (const R*)h.dent_w, afin, (const R*)h.dCm, h.bcap);
+    if (h.nb > 0)
+      k_body_force<R><<<h.nb, 256, 0, s>>>(h.dbodies, h.dX, h.dY, h.dds, afin);
+  } else if (h.nb > 0) {
+    // no correction: no hydrodynamic force
+    k_body_force<R><<<h.nb, 256, 0, s>>>(h.dbodies, h.dX, h.dY, h.dds, (const R*)h.dA0);
+  }
+}
+
+void launch_ib_loop(const Ctx& h, int parity, cudaStream_t s) {
+  switch (h.prec) {
+    case PREC_FP64: ib_loop_t<PREC_FP64>(h, parity, s); break;
+    case PREC_FP32: ib_loop_t<PREC_FP32>(h, parity, s); break;
+    case PREC_FP16_DEV: ib_loop_t<PREC_FP16_DEV>(h, parity, s); break;
+    default: ib_loop_t<PREC_BF16_DEV>(h, parity, s); break;
+  }
+}
+
+template <class R>
+static void body_update_t(const Ctx& h, cudaStream_t s) {
+  k_body_update<<<1, ((h.nb + 31) / 32) * 32, 0, s>>>(h.geom, h.dbodies, h.nb);
+  k_marker_move<R><<<blocks_for(h.nm, 128), 128, 0, s>>>(h.nm, h.dbodies, h.dmbody, h.ddX, h.ddY, h.dX, h.dY,
+                                                         (R*)h.dUx, (R*)h.dUy);
+  band_build_t<R>(h, s);
+}
+
+void launch_body_update(const Ctx& h, cudaStream_t s) {
+  if (h.nb == 0 || !h.any_moving) return;
+  if (h.r_bytes == 8) body_update_t<double>(h, s);
+  else body_update_t<float>(h, s);
+}
+
+}  // namespace ibm

@@ -1,0 +1,139 @@
+// ibm_internal.h -- the library-side state behind an ibm_handle and the
+// launchers each translation unit provides.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ibm.h"
+#include "ibm_device.cuh"
+
+namespace ibm {
+
+// FP64 record of one rigid body on the device (Eqs. 37-42 state).
+struct BodyDev {
+  int kind, m0, m1, pad;
+  double xc[2], u[2], omega, theta;
+  double u_prev[2], omega_prev, theta0;
+  double rho_s, rho_f, volume, inertia, radius, mass;
+  double gravity[2];
+  double F_ib[2], T_ib;     // Eq. 29 sums of the last step (no internal-mass terms)
+};
+
+enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2 };
+
+enum {
+  FIELD_OP_READ_F = 0,
+  FIELD_OP_WRITE_F = 1,
+  FIELD_OP_INIT_EQ = 2,
+  FIELD_OP_MACROS = 3,
+  FIELD_OP_MACRO_OUT = 4,
+  FIELD_OP_REST = 5
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ibm_lattice_desc desc{};
+  Geom geom{};
+  int prec = PREC_FP32;
+  size_t s_bytes = 4;       // bytes per stored population
+  size_t r_bytes = 4;       // bytes per arithmetic value
+  void* f = nullptr;        // [9][ny][nxp] populations, AA layout
+  void* macro = nullptr;    // [3][ny][nx] rho, ux, uy (arithmetic type)
+  int parity = 0;           // 0: natural layout, next step even; 1: swapped, next odd
+
+  // markers (host master copy, FP64)
+  std::vector<double> hX, hY, hds, hdX, hdY, hUx, hUy;
+  std::vector<int> hmbody;
+  std::vector<BodyDev> hbodies;
+  int nm = 0, nb = 0;
+  bool any_moving = false;
+
+  // marker / band device arrays (sized for nm markers, 16 nm band nodes)
+  int mcap = 0, bcap = 0;
+  double *dX = nullptr, *dY = nullptr, *dds = nullptr, *ddX = nullptr, *ddY = nullptr;
+  int* dmbody = nullptr;
+  void *dUx = nullptr, *dUy = nullptr;       // marker velocity (R)
+  void* dW = nullptr;                        // [16 nm] stencil weights (R)
+  int* dnode_of = nullptr;                   // [16 nm] stencil node or -1
+  int* dband_of = nullptr;                   // [16 nm] band index or -1
+  int* dclaim = nullptr;                     // [16 nm]
+  int* dnode2band = nullptr;                 // [ny nx] band index or -1
+  int* dbnode = nullptr;                     // [bcap] node of band entry
+  int* dbcnt = nullptr;                      // [bcap] covering markers
+  int* dent_m = nullptr;                     // [bcap * kBandCap] marker ids (ascending)
+  void* dent_w = nullptr;                    // [bcap * kBandCap] W ds (R)
+  void *dbrho = nullptr, *dbJ0 = nullptr;    // [bcap], [2 bcap] (R)
+  void *dA0 = nullptr, *dA1 = nullptr;       // [2 nm] accumulated momentum deviation (R)
+  void* dCm = nullptr;                       // [3 nm] accumulated second-moment deviation (R)
+  void* dresid = nullptr;                    // [n_corr + 1] (R)
+  int* dctr = nullptr;                       // [0] band count, [1] error bits
+  BodyDev* dbodies = nullptr;
+  bool band_valid = false;
+
+  // CUDA graphs of one step, per parity and macro flag
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+
+  // kernel timing
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  double acc_ms = 0.0;
+  int acc_n = 0;
+
+  // staging for field transfers
+  double* dio = nullptr;
+  size_t io_cap = 0;
+
+  // counters
+  long long launches = 0;   // kernels enqueued by ibm_step
+  long long steps = 0;
+
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+// Number of CUDA kernels one time step launches (matches enqueue_step).
+inline int kernels_per_step(const Ctx& h) {
+  int k = 1;                                       // collide + stream
+  if (h.nm > 0) {
+    const int N = h.desc.n_corr;
+    k += 1 + N + 1 + (N > 0 ? 1 : 0);              // gather, iterations, residual, apply
+    if (h.nb > 0) k += 1;                          // body force / torque
+    if (h.nb > 0 && h.any_moving) k += 2 + 5;      // body update, marker move, band rebuild
+  }
+  return k;
+}
+
+template <class R>
+StepConsts<R> make_consts(const Ctx& h) {
+  StepConsts<R> c;
+  const ibm_lattice_desc& d = h.desc;
+  c.omega = (R)(1.0 / d.tau);
+  c.rho0 = (R)d.rho0;
+  c.inlet_u[0] = (R)d.inlet_u[0];
+  c.inlet_u[1] = (R)d.inlet_u[1];
+  const double uu = d.inlet_u[0] * d.inlet_u[0] + d.inlet_u[1] * d.inlet_u[1];
+  for (int i = 0; i < 9; ++i) {
+    const double w = wgt<double>(i);
+    for (int s = 0; s < 4; ++s)
+      c.wall[s][i] = (R)(6.0 * w * d.rho0 * (cx(i) * d.wall_u[s][0] + cy(i) * d.wall_u[s][1]));
+    const double eu = cx(i) * d.inlet_u[0] + cy(i) * d.inlet_u[1];
+    c.feq_in[i] = (R)(w * d.rho0 * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+  }
+  return c;
+}
+
+// ibm_lbm.cu
+void launch_collide_stream(const Ctx& h, int parity, bool macro, cudaStream_t s);
+void launch_fields(const Ctx& h, int op, const double* dev_in, double* dev_out, cudaStream_t s);
+
+// ibm_ib.cu
+void launch_band_build(const Ctx& h, cudaStream_t s);
+void launch_ib_loop(const Ctx& h, int parity, cudaStream_t s);
+void launch_body_update(const Ctx& h, cudaStream_t s);
+
+}  // namespace ibm

@@ -1,0 +1,377 @@
+"""Thin Python binding of the C ABI in include/ibm.h (argument marshalling
+only; every step of the method runs in the CUDA kernels of libibm.so).
+
+The functions carry the ABI's names.  Arrays are numpy FP64 on the host.
+There is no fallback: if libibm.so cannot be loaded (not built, or no CUDA
+runtime) the first call raises.  With PyTorch present, device memory comes
+from PyTorch's caching allocator and work is enqueued on a PyTorch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+IBM_OK, IBM_ERR_INVALID, IBM_ERR_NOMEM, IBM_ERR_CUDA = 0, 1, 2, 3
+IBM_ERR_BOUNDS, IBM_ERR_DIVERGED, IBM_ERR_TIMEOUT, IBM_WARN_NOT_CONVERGED = 4, 5, 6, 7
+IBM_FP64, IBM_FP32, IBM_FP16_DEV, IBM_BF16_DEV = 0, 1, 2, 3
+PERIODIC, BOUNCEBACK, FREESLIP, INLET_EQ, OUTLET_ZEROGRAD = 0, 1, 2, 3, 4
+BODY_FIXED, BODY_PRESCRIBED, BODY_FREE = 0, 1, 2
+FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_F = 1, 2, 3, 4
+FIELD_BODIES, FIELD_RESIDUAL, FIELD_MARKERS, FIELD_MACRO_INIT = 5, 6, 7, 8
+STEP_DEFAULT, STEP_NO_GRAPH, STEP_TIME_KERNELS, STEP_NO_MACRO = 0, 1, 2, 4
+
+PRECISIONS = {"fp64": IBM_FP64, "fp32": IBM_FP32, "fp16": IBM_FP16_DEV, "bf16": IBM_BF16_DEV}
+
+_STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID", 2: "IBM_ERR_NOMEM", 3: "IBM_ERR_CUDA",
+           4: "IBM_ERR_BOUNDS", 5: "IBM_ERR_DIVERGED", 6: "IBM_ERR_TIMEOUT",
+           7: "IBM_WARN_NOT_CONVERGED"}
+
+SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields",
+           "ibm_write_fields", "ibm_sync", "ibm_kernel_times", "ibm_get_sizes",
+           "ibm_get_counters", "ibm_destroy", "ibm_last_error", "ibm_set_allocator",
+           "ibm_abi_version")
+
+
+class IBMError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("prec", ctypes.c_int), ("bc", ctypes.c_int * 4),
+                ("wall_u", (ctypes.c_double * 2) * 4), ("inlet_u", ctypes.c_double * 2),
+                ("n_corr", ctypes.c_int), ("corr_tol", ctypes.c_double),
+                ("delta_points", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("device", ctypes.c_int)]
+
+
+class BodyDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("xc", ctypes.c_double * 2), ("u", ctypes.c_double * 2),
+                ("omega", ctypes.c_double), ("theta", ctypes.c_double),
+                ("rho_s", ctypes.c_double), ("rho_f", ctypes.c_double),
+                ("volume", ctypes.c_double), ("inertia", ctypes.c_double),
+                ("radius", ctypes.c_double), ("gravity", ctypes.c_double * 2)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                             ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+_torch_hooks = None
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libibm.so (building it first if asked and absent).  Raises when
+    the library is unavailable: there is no CPU fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: build it with paper_1803_09380_gb300.build")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lib.ibm_create_lattice.argtypes = [ctypes.POINTER(LatticeDesc), ctypes.POINTER(vp)]
+        lib.ibm_add_markers.argtypes = [vp, _D, _D, ci, ctypes.POINTER(BodyDesc), ctypes.POINTER(ci)]
+        lib.ibm_step.argtypes = [vp, ci, ctypes.c_uint]
+        lib.ibm_read_fields.argtypes = [vp, ci, _D, ctypes.c_size_t]
+        lib.ibm_write_fields.argtypes = [vp, ci, _D, ctypes.c_size_t]
+        lib.ibm_sync.argtypes = [vp]
+        lib.ibm_kernel_times.argtypes = [vp, _D, ctypes.POINTER(ci)]
+        lib.ibm_get_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ci),
+                                      ctypes.POINTER(ci), ctypes.POINTER(ci)]
+        lib.ibm_get_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_longlong)]
+        lib.ibm_destroy.argtypes = [vp]
+        lib.ibm_last_error.argtypes = [vp]
+        lib.ibm_last_error.restype = ctypes.c_char_p
+        lib.ibm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
+        lib.ibm_abi_version.restype = ci
+        for name in SYMBOLS:
+            if name not in ("ibm_last_error", "ibm_abi_version"):
+                getattr(lib, name).restype = ci
+        _lib = lib
+        return lib
+
+
+def _check(st: int, h, where: str, allow_warn: bool = False) -> int:
+    if st == IBM_OK or (allow_warn and st == IBM_WARN_NOT_CONVERGED):
+        return st
+    msg = load().ibm_last_error(h).decode(errors="replace")
+    raise IBMError(st, where, msg)
+
+
+def ibm_set_allocator(alloc, release, ctx=None):
+    """Install alloc(bytes, device, stream, ctx) / release(ptr, device,
+    stream, ctx) as the library's device allocator (None, None: cudaMalloc)."""
+    lib = load()
+    if alloc is None:
+        return _check(lib.ibm_set_allocator(_ALLOC_FN(), _FREE_FN(), None), None, "ibm_set_allocator")
+    return _check(lib.ibm_set_allocator(alloc, release, ctx), None, "ibm_set_allocator")
+
+
+def use_torch_allocator() -> bool:
+    """Route the library's device allocations through PyTorch's caching
+    allocator.  Returns False when PyTorch CUDA is unavailable."""
+    global _torch_hooks
+    try:
+        import torch
+    except ImportError:
+        return False
+    if not torch.cuda.is_available():
+        return False
+    if _torch_hooks is not None:
+        return True
+
+    def _alloc(nbytes, device, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), int(device), stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, device, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    ibm_set_allocator(hooks[0], hooks[1])
+    _torch_hooks = hooks
+    return True
+
+
+def ibm_create_lattice(nx, ny, tau, rho0=1.0, prec="fp32", bc=(PERIODIC,) * 4, wall_u=None,
+                       inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, stream=None, device=0):
+    """Create a lattice in the rest equilibrium; returns an opaque handle."""
+    lib = load()
+    d = LatticeDesc()
+    d.nx, d.ny, d.tau, d.rho0 = int(nx), int(ny), float(tau), float(rho0)
+    d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    for s in range(4):
+        d.bc[s] = int(bc[s])
+    wu = np.zeros(8) if wall_u is None else np.asarray(wall_u, dtype=np.float64).reshape(8)
+    for s in range(4):
+        d.wall_u[s][0], d.wall_u[s][1] = float(wu[2 * s]), float(wu[2 * s + 1])
+    d.inlet_u[0], d.inlet_u[1] = float(inlet_u[0]), float(inlet_u[1])
+    d.n_corr, d.corr_tol, d.delta_points = int(n_corr), float(corr_tol), 4
+    d.cuda_stream = stream
+    d.device = int(device)
+    h = ctypes.c_void_p()
+    st = lib.ibm_create_lattice(ctypes.byref(d), ctypes.byref(h))
+    _check(st, None, "ibm_create_lattice")
+    return h
+
+
+def ibm_add_markers(h, xy, ds=None, kind=BODY_FIXED, xc=(0.0, 0.0), u=(0.0, 0.0), omega=0.0,
+                    theta=0.0, rho_s=1.0, rho_f=1.0, volume=0.0, inertia=0.0, radius=0.0,
+                    gravity=(0.0, 0.0)) -> int:
+    lib = load()
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+    n = xy.shape[0]
+    dsp = None
+    if ds is not None:
+        ds = np.ascontiguousarray(np.broadcast_to(ds, (n,)), dtype=np.float64)
+        dsp = ds.ctypes.data_as(_D)
+    b = BodyDesc()
+    b.kind = int(kind)
+    b.xc[0], b.xc[1] = float(xc[0]), float(xc[1])
+    b.u[0], b.u[1] = float(u[0]), float(u[1])
+    b.omega, b.theta = float(omega), float(theta)
+    b.rho_s, b.rho_f, b.volume, b.inertia = float(rho_s), float(rho_f), float(volume), float(inertia)
+    b.radius = float(radius)
+    b.gravity[0], b.gravity[1] = float(gravity[0]), float(gravity[1])
+    bid = ctypes.c_int(-1)
+    _check(lib.ibm_add_markers(h, xy.ctypes.data_as(_D), dsp, n, ctypes.byref(b), ctypes.byref(bid)),
+           h, "ibm_add_markers")
+    return bid.value
+
+
+def ibm_step(h, nsteps: int, flags: int = STEP_DEFAULT) -> None:
+    _check(load().ibm_step(h, int(nsteps), int(flags)), h, "ibm_step")
+
+
+def ibm_get_sizes(h):
+    """(nodes, markers, bodies, band_nodes)."""
+    n, m, b, bn = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().ibm_get_sizes(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(b), ctypes.byref(bn)),
+           h, "ibm_get_sizes")
+    return n.value, m.value, b.value, bn.value
+
+
+def _field_shape(h, field, nx, ny, n_corr):
+    if field in (FIELD_RHO, FIELD_UX, FIELD_UY):
+        return (ny, nx)
+    if field == FIELD_F:
+        return (9, ny, nx)
+    if field == FIELD_RESIDUAL:
+        return (n_corr + 1,)
+    _, m, b, _ = ibm_get_sizes(h)
+    if field == FIELD_BODIES:
+        return (b, 9)
+    if field == FIELD_MARKERS:
+        return (m, 2)
+    raise ValueError(f"unknown field {field}")
+
+
+def ibm_read_fields(h, field: int, nx: int, ny: int, n_corr: int = 0, out=None):
+    """Copy a field to a new (or the given) FP64 host array.  Returns
+    (array, status); status is IBM_WARN_NOT_CONVERGED for a residual above
+    corr_tol, otherwise IBM_OK."""
+    shape = _field_shape(h, field, nx, ny, n_corr)
+    if out is None:
+        out = np.empty(shape, dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == shape
+    st = load().ibm_read_fields(h, int(field), out.ctypes.data_as(_D), out.size)
+    st = _check(st, h, "ibm_read_fields", allow_warn=True)
+    return out, st
+
+
+def ibm_write_fields(h, field: int, src) -> None:
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    _check(load().ibm_write_fields(h, int(field), src.ctypes.data_as(_D), src.size), h, "ibm_write_fields")
+
+
+def ibm_sync(h) -> None:
+    _check(load().ibm_sync(h), h, "ibm_sync")
+
+
+def ibm_kernel_times(h):
+    """(total ms, launches) of the collide+stream launches timed since the
+    last call."""
+    ms, n = ctypes.c_double(), ctypes.c_int()
+    _check(load().ibm_kernel_times(h, ctypes.byref(ms), ctypes.byref(n)), h, "ibm_kernel_times")
+    return ms.value, n.value
+
+
+def ibm_get_counters(h):
+    """(kernel launches, steps) since creation."""
+    k, s = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().ibm_get_counters(h, ctypes.byref(k), ctypes.byref(s)), h, "ibm_get_counters")
+    return k.value, s.value
+
+
+def ibm_destroy(h) -> None:
+    if h is not None and h.value:
+        _check(load().ibm_destroy(h), None, "ibm_destroy")
+        h.value = None
+
+
+def ibm_last_error(h=None) -> str:
+    return load().ibm_last_error(h).decode(errors="replace")
+
+
+class Lattice:
+    """Owning wrapper of one handle (context manager).  Uses a PyTorch
+    stream and PyTorch's caching allocator when PyTorch CUDA is present."""
+
+    def __init__(self, nx, ny, tau, rho0=1.0, prec="fp32", bc=(PERIODIC,) * 4, wall_u=None,
+                 inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, device=0, torch_stream=True):
+        self.nx, self.ny, self.n_corr = int(nx), int(ny), int(n_corr)
+        self.prec = prec
+        self._stream = None
+        stream_ptr = None
+        if torch_stream:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    use_torch_allocator()
+                    self._stream = torch.cuda.Stream(device=device)
+                    stream_ptr = self._stream.cuda_stream
+            except ImportError:
+                pass
+        self.h = ibm_create_lattice(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr,
+                                    corr_tol, stream_ptr, device)
+
+    @classmethod
+    def from_case(cls, case, prec="fp32", **kw):
+        lat = cls(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u, case.inlet_u,
+                  case.n_corr, **kw)
+        for b in case.bodies:
+            lat.add_markers(b.xy, b.ds, **b.as_kwargs())
+        return lat
+
+    def add_markers(self, xy, ds=None, **body) -> int:
+        return ibm_add_markers(self.h, xy, ds, **body)
+
+    def step(self, n=1, flags=STEP_DEFAULT):
+        ibm_step(self.h, n, flags)
+
+    def read(self, field, out=None):
+        return ibm_read_fields(self.h, field, self.nx, self.ny, self.n_corr, out)[0]
+
+    def write(self, field, src):
+        ibm_write_fields(self.h, field, src)
+
+    def moments(self):
+        return self.read(FIELD_RHO), self.read(FIELD_UX), self.read(FIELD_UY)
+
+    @property
+    def f(self):
+        return self.read(FIELD_F)
+
+    @f.setter
+    def f(self, value):
+        self.write(FIELD_F, value)
+
+    @property
+    def resid(self):
+        return self.read(FIELD_RESIDUAL)
+
+    @property
+    def bodies(self):
+        return self.read(FIELD_BODIES)
+
+    @property
+    def markers(self):
+        return self.read(FIELD_MARKERS)
+
+    def init_equilibrium(self, rho, ux, uy):
+        shp = (self.ny, self.nx)
+        a = np.stack([np.broadcast_to(rho, shp), np.broadcast_to(ux, shp), np.broadcast_to(uy, shp)])
+        self.write(FIELD_MACRO_INIT, a)
+
+    def sync(self):
+        ibm_sync(self.h)
+
+    def sizes(self):
+        return ibm_get_sizes(self.h)
+
+    def kernel_times(self):
+        return ibm_kernel_times(self.h)
+
+    def counters(self):
+        return ibm_get_counters(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            ibm_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

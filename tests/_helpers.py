@@ -1,0 +1,47 @@
+"""Shared helpers of the parity tests: build the same case on the oracle and
+on the CUDA library, and compare normwise."""
+import numpy as np
+
+import oracle
+from paper_1803_09380_gb300 import ibm
+
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def oracle_lattice(case, n_corr=None):
+    L = oracle.Lattice(case.nx, case.ny, case.tau, case.rho0, case.bc, case.wall_u,
+                       case.inlet_u, case.n_corr if n_corr is None else n_corr)
+    for b in case.bodies:
+        L.add_body(b.xy, b.ds, **b.as_kwargs())
+    return L
+
+
+def gpu_lattice(case, prec, n_corr=None):
+    lat = ibm.Lattice(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u,
+                      case.inlet_u, case.n_corr if n_corr is None else n_corr)
+    for b in case.bodies:
+        lat.add_markers(b.xy, b.ds, **b.as_kwargs())
+    return lat
+
+
+def relerr(a, b):
+    """||a - b||_inf / ||b||_inf (absolute when b is identically zero)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = np.max(np.abs(a - b)) if a.size else 0.0
+    s = np.max(np.abs(b)) if b.size else 0.0
+    return d / s if s > 0 else d
+
+
+def field_errors(gpu, ora, rho0=1.0):
+    """Normwise errors on rho - rho0, u_x, u_y (last corrected state) and on
+    f - w_i (current post-stream populations)."""
+    gr, gx, gy = gpu.moments()
+    orr, ox, oy = ora.moments()
+    fg, fo = gpu.f, ora.f
+    return {
+        "rho": relerr(gr - rho0, orr - rho0),
+        "ux": relerr(gx, ox),
+        "uy": relerr(gy, oy),
+        "f": relerr(fg - W[:, None, None] * rho0, fo - W[:, None, None] * rho0),
+    }

@@ -1,0 +1,267 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+FP64 mode: every field within 1e-12 normwise after the stated number of
+steps (the arithmetic is the same up to summation order: the library uses the
+moment form of the correction, the oracle the nine populations).  FP32 mode:
+steady velocity within 1e-4 of the FP64 oracle.  Sizes span several 32-wide
+tiles with ragged tails; the full 4096^2 Couette lattice is checked against
+the oracle for two steps in the configuration the benchmark times."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_09380_gb300 import ibm
+from paper_1803_09380_gb300 import workloads as wl
+
+from _helpers import field_errors, gpu_lattice, oracle_lattice, relerr
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _run_pair(case, steps, prec="fp64", init=None, n_corr=None):
+    ora = oracle_lattice(case, n_corr)
+    gpu = gpu_lattice(case, prec, n_corr)
+    if init is not None:
+        init(ora, gpu)
+    ora.step(steps)
+    gpu.step(steps)
+    return ora, gpu
+
+
+def _assert_fields(gpu, ora, tol, rho0=1.0):
+    errs = field_errors(gpu, ora, rho0)
+    for k, v in errs.items():
+        assert v < tol, f"{k}: normwise error {v:.3e} >= {tol:.1e} ({errs})"
+
+
+def _random_init(seed):
+    def init(ora, gpu):
+        rho, ux, uy = wl.random_fields(ora.nx, ora.ny, seed)
+        ora.init_equilibrium(rho, ux, uy)
+        f0 = ora.f + wl.random_perturbation(ora.nx, ora.ny, seed + 1, 1e-4)
+        ora.f = f0
+        gpu.f = f0
+    return init
+
+
+# ------------------------------------------------------------------ lattice only
+@pytest.mark.parametrize("steps", [1, 2, 37, 100])
+def test_periodic_collide_stream_fp64(steps):
+    """Random state on a 70 x 45 periodic lattice (three 32-wide tiles, ragged
+    tail), no markers: both AA step kinds, odd and even step counts."""
+    case = wl.Case("periodic", 70, 45, 0.73, n_corr=10)
+    ora, gpu = _run_pair(case, steps, init=_random_init(11))
+    _assert_fields(gpu, ora, TOL64)
+
+
+def test_f_round_trip_is_exact():
+    case = wl.Case("periodic", 37, 9, 0.8)
+    gpu = gpu_lattice(case, "fp64")
+    f0 = np.random.default_rng(4).random((9, 9, 37))
+    gpu.f = f0
+    assert np.array_equal(gpu.f, f0)
+    gpu.step(3)
+    gpu.step(3)
+    assert np.isfinite(gpu.f).all()
+
+
+def test_equilibrium_init_matches_oracle():
+    case = wl.Case("periodic", 40, 33, 0.8)
+    ora, gpu = oracle_lattice(case), gpu_lattice(case, "fp64")
+    rho, ux, uy = wl.random_fields(40, 33, 3)
+    ora.init_equilibrium(rho, ux, uy)
+    gpu.init_equilibrium(rho, ux, uy)
+    assert relerr(gpu.f, ora.f) < 1e-15
+
+
+# ------------------------------------------------------------------ Couette
+def test_couette_64_fp64_100_steps():
+    """64 x 64 Couette (radii 10 and 25, 63 + 157 markers), 100 steps: fields,
+    residual history r^0..r^N and body force/torque."""
+    case = wl.couette_64()
+    ora, gpu = _run_pair(case, 100)
+    _assert_fields(gpu, ora, TOL64)
+    assert relerr(gpu.resid, ora.resid) < 1e-10
+    bg, bo = gpu.bodies, ora.bodies
+    assert relerr(bg[:, 6:9], bo[:, 6:9]) < 1e-10
+
+
+@pytest.mark.parametrize("n,steps", [(48, 60), (100, 25)])
+def test_couette_sizes_fp64(n, steps):
+    case = wl.couette(n)
+    ora, gpu = _run_pair(case, steps)
+    _assert_fields(gpu, ora, TOL64)
+    assert relerr(gpu.resid, ora.resid) < 1e-10
+
+
+@pytest.mark.parametrize("n_corr", [0, 1, 3])
+def test_iteration_counts_fp64(n_corr):
+    case = wl.couette(40)
+    ora, gpu = _run_pair(case, 20, n_corr=n_corr)
+    _assert_fields(gpu, ora, TOL64)
+    assert relerr(gpu.resid, ora.resid) < 1e-10
+
+
+def test_single_marker_and_straight_line_fp64():
+    """Closed-form residuals (5/8 and 1 - 9/64 contractions) reproduced by
+    the library."""
+    n = 16
+    gpu = ibm.Lattice(n, n, 0.8, prec="fp64", n_corr=10)
+    xy = np.stack([np.arange(n) + 0.37, np.full(n, 7.3)], axis=1)
+    gpu.add_markers(xy, np.ones(n), u=(0.01, 0.004))
+    gpu.step(1)
+    r = gpu.resid
+    mag = math.hypot(0.01, 0.004)
+    assert np.all(np.abs(r - mag * (5 / 8) ** np.arange(11)) < 1e-12 * mag)
+    one = ibm.Lattice(n, n, 0.8, prec="fp64", n_corr=10)
+    one.add_markers(np.array([[7.3, 8.6]]), np.array([0.5]), u=(-0.02, 0.013))
+    one.step(1)
+    q = 1 - 9 * 0.5 / 64
+    mag = math.hypot(-0.02, 0.013)
+    assert np.all(np.abs(one.resid - mag * q ** np.arange(11)) < 1e-13 * mag)
+
+
+def test_rest_state_is_exactly_at_rest_on_gpu():
+    """Moment form: at rest j = 0 exactly, so every deviation is exactly zero
+    and u stays bitwise zero (FP64 and FP32)."""
+    for prec in ("fp64", "fp32"):
+        case = wl.couette(48, wall_speed=0.0)
+        gpu = gpu_lattice(case, prec)
+        gpu.step(300)
+        _, ux, uy = gpu.moments()
+        assert np.all(ux == 0) and np.all(uy == 0)
+        assert np.all(gpu.resid == 0)
+
+
+# ------------------------------------------------------------------ walls
+def test_lid_driven_box_with_cylinder_fp64():
+    """Bounce-back on all sides, moving lid, a fixed cylinder inside."""
+    wall_u = np.zeros(8)
+    wall_u[6] = 0.03
+    xy, ds = wl.ring(18.3, 14.6, 5.0)
+    body = wl.Body(xy, ds, wl.BODY_FIXED, xc=(18.3, 14.6), radius=5.0)
+    case = wl.Case("box", 37, 29, 0.7, bc=(1, 1, 1, 1), wall_u=tuple(wall_u), bodies=[body])
+    ora, gpu = _run_pair(case, 60)
+    _assert_fields(gpu, ora, TOL64)
+
+
+def test_channel_inlet_outlet_freeslip_fp64():
+    """Equilibrium inlet, zero-gradient outlet, free-slip walls, cylinder."""
+    case = wl.cylinder(nx=90, ny=41, diameter=10.0, center=(30.0, 20.4), u_in=0.05, re=20.0,
+                       markers=31)
+    ora, gpu = _run_pair(case, 80)
+    _assert_fields(gpu, ora, TOL64)
+    assert relerr(gpu.bodies[:, 6:9], ora.bodies[:, 6:9]) < 1e-10
+
+
+def test_periodic_x_walls_y_fp64():
+    case = wl.Case("chan", 66, 21, 0.9, bc=(0, 0, 1, 2), wall_u=(0, 0, 0, 0, 0.02, 0, 0, 0))
+    ora, gpu = _run_pair(case, 50, init=_random_init(21))
+    _assert_fields(gpu, ora, TOL64)
+
+
+# ------------------------------------------------------------------ moving bodies
+def test_settling_pair_fp64():
+    """Two free disks in a closed box: FP64 Newton-Euler on the GPU vs the
+    oracle, 60 steps (positions, velocities, forces, fields)."""
+    case = wl.settling_pair(nx=64, ny=130, diameter=10.0, density_ratio=1.2, gravity=2e-4)
+    ora, gpu = _run_pair(case, 60)
+    _assert_fields(gpu, ora, TOL64)
+    bg, bo = gpu.bodies, ora.bodies
+    assert np.max(np.abs(bg[:, 0:2] - bo[:, 0:2])) < 1e-10
+    assert relerr(bg[:, 2:4], bo[:, 2:4]) < 1e-10
+    assert relerr(gpu.markers, ora.markers) < 1e-14
+
+
+def test_prescribed_motion_fp64():
+    xy, ds = wl.ring(30.2, 31.7, 6.0)
+    body = wl.Body(xy, ds, wl.BODY_PRESCRIBED, xc=(30.2, 31.7), u=(0.01, -0.004), omega=0.002,
+                   radius=6.0)
+    case = wl.Case("moving", 64, 64, 0.8, bodies=[body])
+    ora, gpu = _run_pair(case, 50)
+    _assert_fields(gpu, ora, TOL64)
+    assert relerr(gpu.markers, ora.markers) < 1e-14
+
+
+# ------------------------------------------------------------------ FP32
+def test_couette_64_fp32_steady_velocity():
+    """FP32 storage and arithmetic: steady velocity within 1e-4 of the FP64
+    oracle (3000 steps, residual drift of the transient below 1e-6)."""
+    case = wl.couette_64()
+    ora, gpu = _run_pair(case, 3000, prec="fp32")
+    _, ox, oy = ora.moments()
+    _, gx, gy = gpu.moments()
+    assert relerr(gx, ox) < 1e-4
+    assert relerr(gy, oy) < 1e-4
+
+
+# ------------------------------------------------------------------ execution modes
+def test_graph_and_eager_paths_are_bitwise_identical():
+    case = wl.couette(40)
+    a = gpu_lattice(case, "fp32")
+    b = gpu_lattice(case, "fp32")
+    a.step(25)
+    b.step(25, ibm.STEP_NO_GRAPH)
+    assert np.array_equal(a.f, b.f)
+    c = gpu_lattice(case, "fp32")
+    c.step(25, ibm.STEP_TIME_KERNELS)
+    assert np.array_equal(a.f, c.f)
+    ms, n = c.kernel_times()
+    assert n == 25 and ms > 0
+
+
+def test_runs_are_deterministic():
+    case = wl.settling_pair(nx=64, ny=130, diameter=10.0, density_ratio=1.2, gravity=2e-4)
+    a = gpu_lattice(case, "fp32")
+    b = gpu_lattice(case, "fp32")
+    a.step(40)
+    b.step(40)
+    assert np.array_equal(a.f, b.f)
+    assert np.array_equal(a.bodies, b.bodies)
+
+
+def test_step_split_matches_single_call():
+    case = wl.couette(40)
+    a = gpu_lattice(case, "fp64")
+    b = gpu_lattice(case, "fp64")
+    a.step(30)
+    for _ in range(3):
+        b.step(10)
+    assert np.array_equal(a.f, b.f)
+
+
+# ------------------------------------------------------------------ full size
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", 2e-5)])
+def test_couette_4096_two_steps_against_oracle(prec, tol):
+    """The 4096^2 Couette lattice (4015 + 10037 markers), two steps from rest
+    as the benchmark launches them (CUDA graph), against the oracle."""
+    case = wl.couette(4096)
+    ora, gpu = _run_pair(case, 2, prec=prec)
+    _, ox, oy = ora.moments()
+    _, gx, gy = gpu.moments()
+    assert relerr(gx, ox) < tol
+    assert relerr(gy, oy) < tol
+    assert relerr(gpu.resid, ora.resid) < (1e-10 if prec == "fp64" else 1e-4)
+
+
+# ------------------------------------------------------------------ errors
+def test_bad_markers_are_rejected():
+    gpu = ibm.Lattice(32, 32, 0.8, prec="fp32", bc=(1, 1, 1, 1))
+    with pytest.raises(ibm.IBMError) as e:
+        gpu.add_markers(np.array([[0.5, 10.0]]), np.array([1.0]))
+    assert e.value.status == ibm.IBM_ERR_INVALID
+    with pytest.raises(ibm.IBMError):
+        gpu.add_markers(np.array([[np.nan, 10.0]]), np.array([1.0]))
+
+
+def test_zero_steps_and_empty_lattice():
+    gpu = ibm.Lattice(8, 8, 0.8, prec="fp32")
+    gpu.step(0)
+    gpu.step(5)
+    rho, ux, uy = gpu.moments()
+    assert np.allclose(rho, 1.0) and np.all(ux == 0)
+    assert gpu.sizes() == (64, 0, 0, 0)
