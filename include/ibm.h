@@ -15,8 +15,9 @@
  *     library (plain cudaMalloc, or the allocator installed with
  *     ibm_set_allocator) and released by ibm_destroy.
  *   - Work is enqueued on the CUDA stream named in the lattice descriptor
- *     (NULL = the legacy default stream).  ibm_step returns once the work is
- *     enqueued; ibm_read_fields synchronises that stream, so asynchronous
+ *     (the correction loop forks onto a private high-priority stream and
+ *     joins back within each step).  ibm_step returns once the work is
+ *     enqueued; ibm_read_fields synchronises the stream, so asynchronous
  *     device errors surface there (and in ibm_destroy / ibm_sync).
  *   - No exception crosses the ABI.  Every call returns an ibm_status;
  *     ibm_last_error(h) gives a message for the last failure on that handle
@@ -86,7 +87,9 @@ typedef struct {
   double corr_tol;            /* 0: always N iterations; > 0: report
                                  IBM_WARN_NOT_CONVERGED when r^N > corr_tol */
   int delta_points;           /* 4 (Eq. 15c); other kernels are not built */
-  void *cuda_stream;          /* cudaStream_t to enqueue on; NULL = default */
+  void *cuda_stream;          /* cudaStream_t to enqueue on; NULL: the library
+                                 creates its own stream, which synchronises
+                                 with the legacy default stream */
   int device;                 /* CUDA device ordinal */
 } ibm_lattice_desc;
 
@@ -164,9 +167,10 @@ ibm_status ibm_write_fields(ibm_handle h, int field, const double *host_src, siz
 /* Blocks until the handle's queued work is done; reports device errors. */
 ibm_status ibm_sync(ibm_handle h);
 
-/* Total device time of the collide+stream launches bracketed since the last
- * call (IBM_STEP_TIME_KERNELS), in milliseconds, and their count; resets
- * the accumulators.  Synchronises the stream. */
+/* Device time of the collide+stream launches bracketed since the last call
+ * (IBM_STEP_TIME_KERNELS), in milliseconds, summed over both launches of a
+ * step (band-free segments and band segments), and the number of time steps
+ * it covers; resets the accumulators.  Synchronises the stream. */
 ibm_status ibm_kernel_times(ibm_handle h, double *ms_total, int *launches);
 
 /* Sizes: nodes, markers, bodies, band nodes (distinct nodes inside some

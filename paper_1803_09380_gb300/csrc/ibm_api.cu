@@ -20,7 +20,8 @@ ibm_free_fn g_free = nullptr;
 void* g_actx = nullptr;
 thread_local std::string t_err;
 
-constexpr int kEventPairs = 4096;
+constexpr int kEventPairs = 4096;     // timed steps held before folding
+constexpr int kEventsPerStep = 4;     // around both collide+stream launches
 
 ibm_status fail(Ctx* h, ibm_status st, const std::string& msg) {
   if (h) h->err = msg; else t_err = msg;
@@ -83,12 +84,13 @@ void destroy_graphs(Ctx& h) {
 
 ibm_status check_device_flags(Ctx* h) {
   if (!h->dctr) return IBM_OK;
-  int ctr[2] = {0, 0};
+  int ctr[CTR_COUNT] = {0, 0, 0, 0};
   IBM_CK(h, cudaMemcpyAsync(ctr, h->dctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
   IBM_CK(h, cudaStreamSynchronize(h->stream));
-  if (ctr[1] & ERR_BAND_CAP) return fail(h, IBM_ERR_BOUNDS, "band node capacity exceeded");
-  if (ctr[1] & ERR_LIST_CAP)
+  if (ctr[CTR_ERR] & ERR_BAND_CAP) return fail(h, IBM_ERR_BOUNDS, "band node capacity exceeded");
+  if (ctr[CTR_ERR] & ERR_LIST_CAP)
     return fail(h, IBM_ERR_BOUNDS, "more than 32 markers cover one node (markers too dense)");
+  if (ctr[CTR_ERR] & ERR_SEG_CAP) return fail(h, IBM_ERR_BOUNDS, "band segment capacity exceeded");
   return IBM_OK;
 }
 
@@ -106,22 +108,44 @@ ibm_status ensure_io(Ctx* h, size_t doubles) {
   return IBM_OK;
 }
 
-// The launch sequence of one time step (ordering on one stream).
+// The launch sequence of one time step.  Without markers: one collide+stream
+// launch.  With markers the step forks: the correction loop runs on the
+// high-priority stream while collide+stream covers every row segment free of
+// band nodes on the main stream; after the join, collide+stream covers the
+// band segments, then moving bodies are advanced and re-binned.
 void enqueue_step(Ctx& h, int parity, bool macro, bool timing) {
-  launch_ib_loop(h, parity, h.stream);
-  launch_body_update(h, h.stream);
-  if (timing && h.ev_used < kEventPairs) cudaEventRecord(h.ev[2 * h.ev_used], h.stream);
-  launch_collide_stream(h, parity, macro, h.stream);
-  if (timing && h.ev_used < kEventPairs) { cudaEventRecord(h.ev[2 * h.ev_used + 1], h.stream); h.ev_used++; }
+  const bool t = timing && h.ev_used < kEventPairs;
+  cudaEvent_t* e = t ? &h.ev[kEventsPerStep * h.ev_used] : nullptr;
+  if (h.nm == 0) {
+    if (t) cudaEventRecord(e[0], h.stream);
+    launch_collide_stream(h, parity, macro, K1_ALL, h.stream);
+    if (t) { cudaEventRecord(e[1], h.stream); cudaEventRecord(e[2], h.stream); cudaEventRecord(e[3], h.stream); }
+  } else {
+    cudaEventRecord(h.ev_fork, h.stream);
+    cudaStreamWaitEvent(h.ib_stream, h.ev_fork, 0);
+    launch_ib_loop(h, parity, h.ib_stream);
+    cudaEventRecord(h.ev_join, h.ib_stream);
+    if (t) cudaEventRecord(e[0], h.stream);
+    launch_collide_stream(h, parity, macro, K1_MAIN, h.stream);
+    if (t) cudaEventRecord(e[1], h.stream);
+    cudaStreamWaitEvent(h.stream, h.ev_join, 0);
+    if (t) cudaEventRecord(e[2], h.stream);
+    launch_collide_stream(h, parity, macro, K1_BAND, h.stream);
+    if (t) cudaEventRecord(e[3], h.stream);
+    launch_body_update(h, h.stream);
+  }
+  if (t) h.ev_used++;
 }
 
 ibm_status fold_events(Ctx* h) {
   if (h->ev_used == 0) return IBM_OK;
   IBM_CK(h, cudaStreamSynchronize(h->stream));
   for (int k = 0; k < h->ev_used; ++k) {
-    float ms = 0.f;
-    IBM_CK(h, cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]));
-    h->acc_ms += ms;
+    float a = 0.f, b = 0.f;
+    cudaEvent_t* e = &h->ev[kEventsPerStep * k];
+    IBM_CK(h, cudaEventElapsedTime(&a, e[0], e[1]));
+    IBM_CK(h, cudaEventElapsedTime(&b, e[2], e[3]));
+    h->acc_ms += a + b;
   }
   h->acc_n += h->ev_used;
   h->ev_used = 0;
@@ -136,12 +160,13 @@ ibm_status upload_markers(Ctx* h) {
                   c.dband_of, c.dclaim, c.dbnode, c.dbcnt, c.dent_m, c.dent_w, c.dbrho, c.dbJ0,
                   c.dA0, c.dA1, c.dCm, c.dbodies};
   IBM_CK(h, cudaStreamSynchronize(c.stream));
-  // clear the node -> band map of the old band before its arrays go away
-  if (c.dbnode && c.dnode2band) {
-    IBM_CK(h, cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)c.geom.nx * c.geom.ny, c.stream));
-    IBM_CK(h, cudaMemsetAsync(c.dctr, 0, 2 * sizeof(int), c.stream));
-    IBM_CK(h, cudaStreamSynchronize(c.stream));
-  }
+  // clear the node -> band map and segment flags of the old band
+  IBM_CK(h, cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)c.geom.nx * c.geom.ny, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dsegflag, 0, sizeof(int) * (size_t)c.nseg_x * c.geom.ny, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dctr, 0, CTR_COUNT * sizeof(int), c.stream));
+  IBM_CK(h, cudaStreamSynchronize(c.stream));
+  dev_free(c, c.dseglist);
+  c.dseglist = nullptr;
   for (void* p : olds) dev_free(c, p);
   c.mcap = M;
   c.bcap = M * kStencil;
@@ -168,6 +193,11 @@ ibm_status upload_markers(Ctx* h) {
   c.dA1 = dev_alloc(c, R * 2 * M);
   c.dCm = dev_alloc(c, R * 3 * M);
   IBM_ALLOC(h, c.dbodies, BodyDev*, c.nb);
+  {
+    const long long nseg = (long long)c.nseg_x * c.geom.ny;
+    c.segcap = (int)(c.bcap < nseg ? c.bcap : nseg);
+    IBM_ALLOC(h, c.dseglist, int*, c.segcap);
+  }
   if (!c.dUx || !c.dUy || !c.dW || !c.dent_w || !c.dbrho || !c.dbJ0 || !c.dA0 || !c.dA1 || !c.dCm)
     return fail(h, IBM_ERR_NOMEM, "device allocation of marker arrays failed");
   IBM_CK(h, cudaMemcpyAsync(c.dX, c.hX.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
@@ -281,6 +311,7 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
   c.geom.ny = d.ny;
   c.geom.nxp = (d.nx + 31) / 32 * 32;
   c.geom.plane = (long long)d.ny * c.geom.nxp;
+  c.nseg_x = c.geom.nxp / kSegW;
   for (int s = 0; s < 4; ++s) c.geom.bc[s] = d.bc[s];
   auto bail = [&](ibm_status st) {
     t_err = c.err;
@@ -298,21 +329,35 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
     }
     c.own_stream = true;
   }
+  {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    c.ib_prio = hi;   // numerically lowest = highest priority
+    if (cudaStreamCreateWithPriority(&c.ib_stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      c.err = "creating the correction-loop stream or its events failed";
+      return bail(IBM_ERR_CUDA);
+    }
+  }
   ibm_status st = IBM_OK;
   do {
     c.f = dev_alloc(c, c.s_bytes * 9 * (size_t)c.geom.plane);
     c.macro = dev_alloc(c, c.r_bytes * 3 * (size_t)d.nx * d.ny);
     c.dnode2band = (int*)dev_alloc(c, sizeof(int) * (size_t)d.nx * d.ny);
-    c.dctr = (int*)dev_alloc(c, 2 * sizeof(int));
+    c.dctr = (int*)dev_alloc(c, CTR_COUNT * sizeof(int));
+    c.dsegflag = (int*)dev_alloc(c, sizeof(int) * (size_t)c.nseg_x * d.ny);
     c.dresid = dev_alloc(c, c.r_bytes * (d.n_corr + 1));
-    if (!c.f || !c.macro || !c.dnode2band || !c.dctr || !c.dresid) {
+    if (!c.f || !c.macro || !c.dnode2band || !c.dctr || !c.dresid || !c.dsegflag) {
       c.err = "device allocation of the lattice failed";
       st = IBM_ERR_NOMEM;
       break;
     }
     if (cudaMemsetAsync(c.f, 0, c.s_bytes * 9 * (size_t)c.geom.plane, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)d.nx * d.ny, c.stream) != cudaSuccess ||
-        cudaMemsetAsync(c.dctr, 0, 2 * sizeof(int), c.stream) != cudaSuccess ||
+        cudaMemsetAsync(c.dctr, 0, CTR_COUNT * sizeof(int), c.stream) != cudaSuccess ||
+        cudaMemsetAsync(c.dsegflag, 0, sizeof(int) * (size_t)c.nseg_x * d.ny, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dresid, 0, c.r_bytes * (d.n_corr + 1), c.stream) != cudaSuccess) {
       c.err = std::string("device memset failed: ") + cudaGetErrorString(cudaGetLastError());
       st = IBM_ERR_CUDA;
@@ -434,7 +479,7 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
     const bool timing = (flags & IBM_STEP_TIME_KERNELS) != 0;
     const bool use_graph = !(flags & (IBM_STEP_NO_GRAPH | IBM_STEP_TIME_KERNELS));
     if (timing && c.ev.empty()) {
-      c.ev.resize(2 * kEventPairs);
+      c.ev.resize(kEventsPerStep * kEventPairs);
       for (auto& e : c.ev) IBM_CK(h, cudaEventCreate(&e));
     }
     if (c.nm > 0 && !c.band_valid) {
@@ -617,14 +662,14 @@ ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodi
   if (markers) *markers = h->nm;
   if (bodies) *bodies = h->nb;
   if (band_nodes) {
-    int ctr[2] = {0, 0};
+    int ctr[CTR_COUNT] = {0, 0, 0, 0};
     if (h->nm > 0 && !h->band_valid) {
       launch_band_build(*h, h->stream);
       h->band_valid = true;
     }
     IBM_CK(h, cudaMemcpyAsync(ctr, h->dctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
     IBM_CK(h, cudaStreamSynchronize(h->stream));
-    *band_nodes = h->nm > 0 ? ctr[0] : 0;
+    *band_nodes = h->nm > 0 ? ctr[CTR_NBAND] : 0;
   }
   return IBM_OK;
 }
@@ -650,6 +695,9 @@ ibm_status ibm_destroy(ibm_handle h) {
     std::vector<void*> all = h->allocs;
     for (void* p : all) dev_free(*h, p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->ib_stream) cudaStreamDestroy(h->ib_stream);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
   }
   delete h;
   return st;

@@ -55,11 +55,15 @@ template <> struct AtomicBits<double> {
 // One thread per (marker, stencil slot).  Clearing the previous band, then
 // claim / allocate / fill / sort in separate launches (kernel boundaries are
 // the only ordering used, so no thread ever waits on another).
-__global__ void k_band_clear(const int* __restrict__ ctr, const int* __restrict__ bnode,
-                             int* __restrict__ node2band, int bcap) {
+__global__ void k_band_clear(Geom g, const int* __restrict__ ctr, const int* __restrict__ bnode,
+                             int* __restrict__ node2band, int* __restrict__ segflag, int nseg_x,
+                             int bcap) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nb = min(ctr[0], bcap);
-  if (b < nb) node2band[bnode[b]] = -1;
+  const int nb = min(ctr[CTR_NBAND], bcap);
+  if (b >= nb) return;
+  const int n = bnode[b];
+  node2band[n] = -1;
+  segflag[(n / g.nx) * nseg_x + (n % g.nx) / kSegW] = 0;
 }
 
 template <class R>
@@ -90,14 +94,28 @@ __global__ void k_band_alloc(int M, const int* __restrict__ node_of, const int* 
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= M * kStencil || !claim[t]) return;
   const int n = node_of[t];
-  const int b = atomicAdd(&ctr[0], 1);
+  const int b = atomicAdd(&ctr[CTR_NBAND], 1);
   if (b < bcap) {
     bnode[b] = n;
     bcnt[b] = 0;
     node2band[n] = b;
   } else {
-    atomicOr(&ctr[1], ERR_BAND_CAP);
+    atomicOr(&ctr[CTR_ERR], ERR_BAND_CAP);
   }
+}
+
+// Row segments (32 nodes) holding a band node: flagged once, listed once.
+__global__ void k_band_segments(Geom g, const int* __restrict__ bnode, int* __restrict__ segflag,
+                                int* __restrict__ seglist, int* __restrict__ ctr, int nseg_x, int bcap,
+                                int segcap) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= min(ctr[CTR_NBAND], bcap)) return;
+  const int n = bnode[b];
+  const int seg = (n / g.nx) * nseg_x + (n % g.nx) / kSegW;
+  if (atomicCAS(&segflag[seg], 0, 1) != 0) return;
+  const int k = atomicAdd(&ctr[CTR_NSEG], 1);
+  if (k < segcap) seglist[k] = seg;
+  else atomicOr(&ctr[CTR_ERR], ERR_SEG_CAP);
 }
 
 template <class R>
@@ -117,7 +135,7 @@ __global__ void k_band_fill(int M, const int* __restrict__ node_of, const R* __r
     ent_m[(long long)b * kBandCap + pos] = l;
     ent_w[(long long)b * kBandCap + pos] = (R)((double)W[t] * ds[l]);
   } else {
-    atomicOr(&ctr[1], ERR_LIST_CAP);
+    atomicOr(&ctr[CTR_ERR], ERR_LIST_CAP);
   }
 }
 
@@ -125,7 +143,7 @@ template <class R>
 __global__ void k_band_sort(const int* __restrict__ ctr, int* __restrict__ bcnt,
                             int* __restrict__ ent_m, R* __restrict__ ent_w, int bcap) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= min(ctr[0], bcap)) return;
+  if (b >= min(ctr[CTR_NBAND], bcap)) return;
   const int n = min(bcnt[b], kBandCap);
   bcnt[b] = n;
   int* m = ent_m + (long long)b * kBandCap;
@@ -149,7 +167,7 @@ __global__ void k_ib_gather(Geom g, StepConsts<typename Prec<P>::R> c,
                             int bcap) {
   typedef typename Prec<P>::R R;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= min(ctr[0], bcap)) return;
+  if (b >= min(ctr[CTR_NBAND], bcap)) return;
   const int n = bnode[b];
   const int x = n % g.nx, y = n / g.nx;
   R p[9], rho, jx, jy;
@@ -256,7 +274,7 @@ __global__ void k_ib_apply(Geom g, StepConsts<typename Prec<P>::R> c, typename P
                            const typename Prec<P>::R* __restrict__ Cm, int bcap) {
   typedef typename Prec<P>::R R;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= min(ctr[0], bcap)) return;
+  if (b >= min(ctr[CTR_NBAND], bcap)) return;
   R jx = R(0), jy = R(0), pxx = R(0), pxy = R(0), pyy = R(0);
   const int cnt = bcnt[b];
   const long long o = (long long)b * kBandCap;
@@ -395,8 +413,9 @@ template <class R>
 static void band_build_t(const Ctx& h, cudaStream_t s) {
   const int T = h.nm * kStencil;
   if (T == 0) return;
-  k_band_clear<<<blocks_for(h.bcap, 256), 256, 0, s>>>(h.dctr, h.dbnode, h.dnode2band, h.bcap);
-  cudaMemsetAsync(h.dctr, 0, sizeof(int), s);
+  k_band_clear<<<blocks_for(h.bcap, 256), 256, 0, s>>>(h.geom, h.dctr, h.dbnode, h.dnode2band,
+                                                        h.dsegflag, h.nseg_x, h.bcap);
+  cudaMemsetAsync(h.dctr, 0, 2 * sizeof(int), s);   // band nodes, band segments
   k_band_claim<R><<<blocks_for(T, 256), 256, 0, s>>>(h.geom, h.nm, h.dX, h.dY, (R*)h.dW, h.dnode_of,
                                                       h.dnode2band, h.dclaim);
   k_band_alloc<<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, h.dclaim, h.dnode2band, h.dbnode,
@@ -404,6 +423,8 @@ static void band_build_t(const Ctx& h, cudaStream_t s) {
   k_band_fill<R><<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, (const R*)h.dW, h.dds, h.dnode2band,
                                                      h.dband_of, h.dbcnt, h.dent_m, (R*)h.dent_w, h.dctr);
   k_band_sort<R><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.dctr, h.dbcnt, h.dent_m, (R*)h.dent_w, h.bcap);
+  k_band_segments<<<blocks_for(h.bcap, 256), 256, 0, s>>>(h.geom, h.dbnode, h.dsegflag, h.dseglist, h.dctr,
+                                                          h.nseg_x, h.bcap, h.segcap);
 }
 
 void launch_band_build(const Ctx& h, cudaStream_t s) {
@@ -417,44 +438,49 @@ static void ib_loop_t(const Ctx& h, int parity, cudaStream_t s) {
   typedef typename Prec<P>::R R;
   if (h.nm == 0) return;
   const int N = h.desc.n_corr;
+  const int pr = h.ib_prio;
   StepConsts<R> c = make_consts<R>(h);
   S* A = (S*)h.f;
   cudaMemsetAsync(h.dresid, 0, sizeof(R) * (N + 1), s);
-  k_ib_gather<P><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.geom, c, A, parity, h.dctr, h.dbnode,
-                                                         (R*)h.dbrho, (R*)h.dbJ0, h.bcap);
-  const unsigned gridM = blocks_for((long long)h.nm * kStencil, 256);
+  launch_prio(k_ib_gather<P>, dim3(blocks_for(h.bcap, 128)), dim3(128), s, pr, h.geom, c, (const S*)A,
+              parity, (const int*)h.dctr, (const int*)h.dbnode, (R*)h.dbrho, (R*)h.dbJ0, h.bcap);
+  const dim3 gridM(blocks_for((long long)h.nm * kStencil, 256));
   R* Acc[2] = {(R*)h.dA0, (R*)h.dA1};
   R* resid = (R*)h.dresid;
+  const int* band_of = h.dband_of;
+  const R* W = (const R*)h.dW;
+  const R* brho = (const R*)h.dbrho;
+  const R* bJ = (const R*)h.dbJ0;
+  const int* bcnt = h.dbcnt;
+  const int* ent_m = h.dent_m;
+  const R* ent_w = (const R*)h.dent_w;
+  const R* Ux = (const R*)h.dUx;
+  const R* Uy = (const R*)h.dUy;
+  R* Cm = (R*)h.dCm;
   for (int n = 0; n < N; ++n) {
     const R* ain = Acc[n & 1];
     R* aout = Acc[(n + 1) & 1];
     if (n == 0)
-      k_ib_iterate<R, true, true><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
-          (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, ain, aout, (R*)h.dCm,
-          (const R*)h.dUx, (const R*)h.dUy, resid + n);
+      launch_prio(k_ib_iterate<R, true, true>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
+                  ent_m, ent_w, ain, aout, Cm, Ux, Uy, resid + n);
     else
-      k_ib_iterate<R, false, true><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
-          (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, ain, aout, (R*)h.dCm,
-          (const R*)h.dUx, (const R*)h.dUy, resid + n);
+      launch_prio(k_ib_iterate<R, false, true>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
+                  ent_m, ent_w, ain, aout, Cm, Ux, Uy, resid + n);
   }
   const R* afin = Acc[N & 1];
+  R* none = nullptr;
   if (N == 0)
-    k_ib_iterate<R, true, false><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
-        (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, afin, nullptr, nullptr,
-        (const R*)h.dUx, (const R*)h.dUy, resid + N);
+    launch_prio(k_ib_iterate<R, true, false>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
+                ent_m, ent_w, afin, none, none, Ux, Uy, resid + N);
   else
-    k_ib_iterate<R, false, false><<<gridM, 256, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, (const R*)h.dbrho,
-        (const R*)h.dbJ0, h.dbcnt, h.dent_m, (const R*)h.dent_w, afin, nullptr, nullptr,
-        (const R*)h.dUx, (const R*)h.dUy, resid + N);
-  if (N > 0) {
-    k_ib_apply<P><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.geom, c, A, parity, h.dctr, h.dbnode, h.dbcnt,
-        h.dent_m, (const R*)h.dent_w, afin, (const R*)h.dCm, h.bcap);
-    if (h.nb > 0)
-      k_body_force<R><<<h.nb, 256, 0, s>>>(h.dbodies, h.dX, h.dY, h.dds, afin);
-  } else if (h.nb > 0) {
-    // no correction: no hydrodynamic force
-    k_body_force<R><<<h.nb, 256, 0, s>>>(h.dbodies, h.dX, h.dY, h.dds, (const R*)h.dA0);
-  }
+    launch_prio(k_ib_iterate<R, false, false>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
+                ent_m, ent_w, afin, none, none, Ux, Uy, resid + N);
+  if (N > 0)
+    launch_prio(k_ib_apply<P>, dim3(blocks_for(h.bcap, 128)), dim3(128), s, pr, h.geom, c, A, parity,
+                (const int*)h.dctr, (const int*)h.dbnode, bcnt, ent_m, ent_w, afin, (const R*)Cm, h.bcap);
+  if (h.nb > 0)
+    launch_prio(k_body_force<R>, dim3(h.nb), dim3(256), s, pr, h.dbodies, (const double*)h.dX,
+                (const double*)h.dY, (const double*)h.dds, afin);
 }
 
 void launch_ib_loop(const Ctx& h, int parity, cudaStream_t s) {

@@ -22,7 +22,16 @@ struct BodyDev {
   double F_ib[2], T_ib;     // Eq. 29 sums of the last step (no internal-mass terms)
 };
 
-enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2 };
+enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4 };
+
+// Device counters: band nodes, band row segments, error bits.
+enum { CTR_NBAND = 0, CTR_NSEG = 1, CTR_ERR = 2, CTR_COUNT = 4 };
+
+// Collide+stream launch modes: every node; every 32-node row segment
+// without a band node (runs while the correction loop runs); the band
+// segments only (after the correction).
+enum { K1_ALL = 0, K1_MAIN = 1, K1_BAND = 2 };
+constexpr int kSegW = 32;
 
 enum {
   FIELD_OP_READ_F = 0,
@@ -37,6 +46,9 @@ struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t ib_stream = nullptr;   // high-priority stream of the correction loop
+  int ib_prio = 0;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ibm_lattice_desc desc{};
   Geom geom{};
   int prec = PREC_FP32;
@@ -71,16 +83,20 @@ struct Ctx {
   void *dA0 = nullptr, *dA1 = nullptr;       // [2 nm] accumulated momentum deviation (R)
   void* dCm = nullptr;                       // [3 nm] accumulated second-moment deviation (R)
   void* dresid = nullptr;                    // [n_corr + 1] (R)
-  int* dctr = nullptr;                       // [0] band count, [1] error bits
+  int* dctr = nullptr;                       // CTR_* counters
+  int nseg_x = 0;                            // 32-node segments per row
+  int segcap = 0;
+  int* dsegflag = nullptr;                   // [ny][nseg_x] 1 if the segment has a band node
+  int* dseglist = nullptr;                   // [segcap] band segments
   BodyDev* dbodies = nullptr;
   bool band_valid = false;
 
   // CUDA graphs of one step, per parity and macro flag
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 
-  // kernel timing
+  // kernel timing: kEventsPerStep events per timed step
   std::vector<cudaEvent_t> ev;
-  int ev_used = 0;
+  int ev_used = 0;                           // timed steps recorded
   double acc_ms = 0.0;
   int acc_n = 0;
 
@@ -101,9 +117,10 @@ inline int kernels_per_step(const Ctx& h) {
   int k = 1;                                       // collide + stream
   if (h.nm > 0) {
     const int N = h.desc.n_corr;
+    k += 1;                                        // collide + stream of the band segments
     k += 1 + N + 1 + (N > 0 ? 1 : 0);              // gather, iterations, residual, apply
     if (h.nb > 0) k += 1;                          // body force / torque
-    if (h.nb > 0 && h.any_moving) k += 2 + 5;      // body update, marker move, band rebuild
+    if (h.nb > 0 && h.any_moving) k += 2 + 6;      // body update, marker move, band rebuild
   }
   return k;
 }
@@ -127,8 +144,27 @@ StepConsts<R> make_consts(const Ctx& h) {
   return c;
 }
 
+// Kernel launch with a scheduling priority attribute (kept by stream capture,
+// so the correction loop's small kernels are dispatched ahead of the waiting
+// blocks of the concurrent collide+stream launch).
+template <typename... KArgs, typename... Args>
+inline void launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, int prio,
+                        Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ibm_lbm.cu
-void launch_collide_stream(const Ctx& h, int parity, bool macro, cudaStream_t s);
+void launch_collide_stream(const Ctx& h, int parity, bool macro, int mode, cudaStream_t s);
 void launch_fields(const Ctx& h, int op, const double* dev_in, double* dev_out, cudaStream_t s);
 
 // ibm_ib.cu

@@ -5,12 +5,18 @@
 //
 // Collide+stream is HBM-bound: every node reads its nine populations once and
 // writes them once (18 s bytes per node update, s = bytes per stored
-// population).  One thread per node, one block row segment per row, so warps
-// read and write consecutive x.  The even step touches only the thread's own
-// node.  The odd step reads each population from the neighbour it streams
-// from and writes it to the neighbour it streams to.  Nodes on a
-// non-periodic side, and the two columns before an outlet, take a per-node
-// path through the location rules of ibm_device.cuh.
+// population).  One thread per node, warps on 32 consecutive x of a row.  The
+// even step touches only the thread's own node.  The odd step reads each
+// population from the neighbour it streams from and writes it to the
+// neighbour it streams to.  Nodes on a non-periodic side, and the two
+// columns before an outlet, take a per-node path through the location rules
+// of ibm_device.cuh.
+//
+// In the AA pattern every slot read or written during a step belongs to
+// exactly one node, so the nodes of a step can be split in any way.  A step
+// with immersed markers is split into the row segments without band nodes
+// (launched while the correction loop runs on another stream: the loop only
+// touches band-node slots) and the band segments (launched after it).
 #include "ibm_internal.h"
 
 namespace ibm {
@@ -39,13 +45,10 @@ __device__ __forceinline__ void write_macro(R* mac, long long n, long long k, R 
 // ------------------------------------------------------------------ even step
 // Reads A[i][x], writes f*_i to A[opp(i)][x]: purely node-local.
 template <int P, bool MACRO>
-__global__ void __launch_bounds__(256) k_even(Geom g, StepConsts<typename Prec<P>::R> c,
-                                              typename Prec<P>::S* __restrict__ A,
-                                              typename Prec<P>::R* __restrict__ mac) {
+__device__ __forceinline__ void even_node(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                          typename Prec<P>::S* __restrict__ A,
+                                          typename Prec<P>::R* __restrict__ mac, int x, int y) {
   typedef typename Prec<P>::R R;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= g.nx) return;
   const long long base = (long long)y * g.nxp + x;
   R p[9], ps[9], rho, jx, jy;
 #pragma unroll
@@ -100,13 +103,10 @@ __device__ void odd_boundary(const Geom& g, const StepConsts<typename Prec<P>::R
 }
 
 template <int P, bool MACRO>
-__global__ void __launch_bounds__(256) k_odd(Geom g, StepConsts<typename Prec<P>::R> c,
-                                             typename Prec<P>::S* __restrict__ A,
-                                             typename Prec<P>::R* __restrict__ mac) {
+__device__ __forceinline__ void odd_node(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                         typename Prec<P>::S* __restrict__ A,
+                                         typename Prec<P>::R* __restrict__ mac, int x, int y) {
   typedef typename Prec<P>::R R;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= g.nx) return;
   if (needs_boundary_path(g, x, y)) {
     odd_boundary<P, MACRO>(g, c, A, mac, x, y);
     return;
@@ -130,6 +130,39 @@ __global__ void __launch_bounds__(256) k_odd(Geom g, StepConsts<typename Prec<P>
     const int ty = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
     A[i * g.plane + (long long)ty * g.nxp + tx] = Prec<P>::st(ps[i], i);
   }
+}
+
+// One time step of collide+stream.  PAR 0: even step, 1: odd step.
+// MODE K1_ALL: one thread per node of the grid (nx/256 blocks, ny rows).
+// MODE K1_MAIN: the same grid, but every warp whose 32-node segment holds a
+//   band node returns at once (those nodes wait for the correction loop).
+// MODE K1_BAND: persistent warps walk the list of band segments.
+template <int P, int PAR, bool MACRO, int MODE>
+__global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
+                                                        typename Prec<P>::S* __restrict__ A,
+                                                        typename Prec<P>::R* __restrict__ mac,
+                                                        const int* __restrict__ segflag,
+                                                        const int* __restrict__ seglist,
+                                                        const int* __restrict__ ctr, int nseg_x) {
+  if (MODE == K1_BAND) {
+    const int nseg = ctr[CTR_NSEG];
+    const int lane = threadIdx.x & (kSegW - 1);
+    const int nw = (gridDim.x * blockDim.x) / kSegW;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / kSegW; k < nseg; k += nw) {
+      const int seg = seglist[k];
+      const int y = seg / nseg_x, x = (seg % nseg_x) * kSegW + lane;
+      if (x >= g.nx) continue;
+      if (PAR == 0) even_node<P, MACRO>(g, c, A, mac, x, y);
+      else odd_node<P, MACRO>(g, c, A, mac, x, y);
+    }
+    return;
+  }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= g.nx) return;
+  if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) return;
+  if (PAR == 0) even_node<P, MACRO>(g, c, A, mac, x, y);
+  else odd_node<P, MACRO>(g, c, A, mac, x, y);
 }
 
 // ------------------------------------------------------------------ fields
@@ -217,29 +250,48 @@ __global__ void k_macro_to_double(long long n, const R* __restrict__ mac, double
 // ------------------------------------------------------------------ launchers
 static dim3 row_grid(const Geom& g, int bs) { return dim3((g.nx + bs - 1) / bs, g.ny); }
 
-template <int P>
-static void launch_collide_stream_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
+template <int P, int PAR, bool MACRO>
+static void launch_k1(const Ctx& h, const StepConsts<typename Prec<P>::R>& c, int mode, cudaStream_t s) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
-  StepConsts<R> c = make_consts<R>(h);
   S* A = (S*)h.f;
   R* mac = (R*)h.macro;
-  dim3 grid = row_grid(h.geom, 256);
-  if (parity == 0) {
-    if (macro) k_even<P, true><<<grid, 256, 0, s>>>(h.geom, c, A, mac);
-    else k_even<P, false><<<grid, 256, 0, s>>>(h.geom, c, A, mac);
+  if (mode == K1_BAND) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int need = (h.segcap * kSegW + 255) / 256;
+    const int blocks = need < 4 * sms ? (need > 0 ? need : 1) : 4 * sms;
+    k_collide_stream<P, PAR, MACRO, K1_BAND><<<blocks, 256, 0, s>>>(h.geom, c, A, mac, h.dsegflag,
+                                                                    h.dseglist, h.dctr, h.nseg_x);
+  } else if (mode == K1_MAIN) {
+    k_collide_stream<P, PAR, MACRO, K1_MAIN><<<row_grid(h.geom, 256), 256, 0, s>>>(
+        h.geom, c, A, mac, h.dsegflag, h.dseglist, h.dctr, h.nseg_x);
   } else {
-    if (macro) k_odd<P, true><<<grid, 256, 0, s>>>(h.geom, c, A, mac);
-    else k_odd<P, false><<<grid, 256, 0, s>>>(h.geom, c, A, mac);
+    k_collide_stream<P, PAR, MACRO, K1_ALL><<<row_grid(h.geom, 256), 256, 0, s>>>(
+        h.geom, c, A, mac, h.dsegflag, h.dseglist, h.dctr, h.nseg_x);
   }
 }
 
-void launch_collide_stream(const Ctx& h, int parity, bool macro, cudaStream_t s) {
+template <int P>
+static void launch_collide_stream_t(const Ctx& h, int parity, bool macro, int mode, cudaStream_t s) {
+  typedef typename Prec<P>::R R;
+  StepConsts<R> c = make_consts<R>(h);
+  if (parity == 0) {
+    if (macro) launch_k1<P, 0, true>(h, c, mode, s);
+    else launch_k1<P, 0, false>(h, c, mode, s);
+  } else {
+    if (macro) launch_k1<P, 1, true>(h, c, mode, s);
+    else launch_k1<P, 1, false>(h, c, mode, s);
+  }
+}
+
+void launch_collide_stream(const Ctx& h, int parity, bool macro, int mode, cudaStream_t s) {
   switch (h.prec) {
-    case PREC_FP64: launch_collide_stream_t<PREC_FP64>(h, parity, macro, s); break;
-    case PREC_FP32: launch_collide_stream_t<PREC_FP32>(h, parity, macro, s); break;
-    case PREC_FP16_DEV: launch_collide_stream_t<PREC_FP16_DEV>(h, parity, macro, s); break;
-    default: launch_collide_stream_t<PREC_BF16_DEV>(h, parity, macro, s); break;
+    case PREC_FP64: launch_collide_stream_t<PREC_FP64>(h, parity, macro, mode, s); break;
+    case PREC_FP32: launch_collide_stream_t<PREC_FP32>(h, parity, macro, mode, s); break;
+    case PREC_FP16_DEV: launch_collide_stream_t<PREC_FP16_DEV>(h, parity, macro, mode, s); break;
+    default: launch_collide_stream_t<PREC_BF16_DEV>(h, parity, macro, mode, s); break;
   }
 }
 

@@ -32,10 +32,14 @@ def _run_pair(case, steps, prec="fp64", init=None, n_corr=None):
     return ora, gpu
 
 
-def _assert_fields(gpu, ora, tol, rho0=1.0):
+def _assert_fields(gpu, ora, tol, rho0=1.0, tol_dev=None):
+    """rho, u, f within tol; f - w_i within tol_dev (default 10 tol, the
+    oracle's rounding floor on the deviations, see field_errors)."""
     errs = field_errors(gpu, ora, rho0)
+    lim = {"fdev": 10 * tol if tol_dev is None else tol_dev}
     for k, v in errs.items():
-        assert v < tol, f"{k}: normwise error {v:.3e} >= {tol:.1e} ({errs})"
+        t = lim.get(k, tol)
+        assert v < t, f"{k}: normwise error {v:.3e} >= {t:.1e} ({errs})"
 
 
 def _random_init(seed):
@@ -165,12 +169,22 @@ def test_periodic_x_walls_y_fp64():
 
 
 # ------------------------------------------------------------------ moving bodies
+# Moving bodies: velocities are ~1e-3 after 60 steps, so the oracle's absolute
+# rounding floor on the corrections (~eps w_0 per marker iteration, random-walk
+# accumulated over 600 iterations: ~5e-15) is ~1e-12..1e-11 relative to u;
+# the explicit internal-mass term feeds force differences back with gain
+# 1/(1 - rho_f/rho_s).  Tolerance 1e-10 on u and f - w_i.
+TOL_MOVING = 1e-10
+
+
 def test_settling_pair_fp64():
     """Two free disks in a closed box: FP64 Newton-Euler on the GPU vs the
     oracle, 60 steps (positions, velocities, forces, fields)."""
     case = wl.settling_pair(nx=64, ny=130, diameter=10.0, density_ratio=1.2, gravity=2e-4)
     ora, gpu = _run_pair(case, 60)
-    _assert_fields(gpu, ora, TOL64)
+    errs = field_errors(gpu, ora)
+    assert errs["rho"] < TOL64 and errs["f"] < TOL64, errs
+    assert max(errs["ux"], errs["uy"], errs["fdev"]) < TOL_MOVING, errs
     bg, bo = gpu.bodies, ora.bodies
     assert np.max(np.abs(bg[:, 0:2] - bo[:, 0:2])) < 1e-10
     assert relerr(bg[:, 2:4], bo[:, 2:4]) < 1e-10
@@ -183,7 +197,7 @@ def test_prescribed_motion_fp64():
                    radius=6.0)
     case = wl.Case("moving", 64, 64, 0.8, bodies=[body])
     ora, gpu = _run_pair(case, 50)
-    _assert_fields(gpu, ora, TOL64)
+    _assert_fields(gpu, ora, TOL64, tol_dev=TOL_MOVING)
     assert relerr(gpu.markers, ora.markers) < 1e-14
 
 
