@@ -168,15 +168,17 @@ ibm_status ibm_write_fields(ibm_handle h, int field, const double *host_src, siz
 ibm_status ibm_sync(ibm_handle h);
 
 /* Device time of the collide+stream launches bracketed since the last call
- * (IBM_STEP_TIME_KERNELS), in milliseconds, summed over both launches of a
- * step (band-free segments and band segments), and the number of time steps
- * it covers; resets the accumulators.  Synchronises the stream. */
+ * (IBM_STEP_TIME_KERNELS), in milliseconds, and their count; resets the
+ * accumulators.  With markers the bracketed launch covers the band-free row
+ * segments (see ibm_get_sizes).  Synchronises the stream. */
 ibm_status ibm_kernel_times(ibm_handle h, double *ms_total, int *launches);
 
-/* Sizes: nodes, markers, bodies, band nodes (distinct nodes inside some
- * marker support) of the current state; any pointer may be NULL. */
+/* Sizes of the current state: nodes, markers, bodies, band nodes (distinct
+ * nodes inside some marker support) and band segments (32-node row segments
+ * holding a band node, which the correction kernel streams itself); any
+ * pointer may be NULL. */
 ibm_status ibm_get_sizes(ibm_handle h, long long *nodes, int *markers, int *bodies,
-                         int *band_nodes);
+                         int *band_nodes, int *band_segments);
 
 /* Counters since creation: CUDA kernels the library enqueued for ibm_step
  * (a CUDA-graph replay counts the kernels it contains) and time steps taken.

@@ -21,7 +21,7 @@ void* g_actx = nullptr;
 thread_local std::string t_err;
 
 constexpr int kEventPairs = 4096;     // timed steps held before folding
-constexpr int kEventsPerStep = 4;     // around both collide+stream launches
+constexpr int kEventsPerStep = 2;     // around the main collide+stream launch
 
 ibm_status fail(Ctx* h, ibm_status st, const std::string& msg) {
   if (h) h->err = msg; else t_err = msg;
@@ -91,6 +91,8 @@ ibm_status check_device_flags(Ctx* h) {
   if (ctr[CTR_ERR] & ERR_LIST_CAP)
     return fail(h, IBM_ERR_BOUNDS, "more than 32 markers cover one node (markers too dense)");
   if (ctr[CTR_ERR] & ERR_SEG_CAP) return fail(h, IBM_ERR_BOUNDS, "band segment capacity exceeded");
+  if (ctr[CTR_ERR] & ERR_BARRIER)
+    return fail(h, IBM_ERR_TIMEOUT, "the correction-loop grid barrier timed out");
   return IBM_OK;
 }
 
@@ -109,29 +111,27 @@ ibm_status ensure_io(Ctx* h, size_t doubles) {
 }
 
 // The launch sequence of one time step.  Without markers: one collide+stream
-// launch.  With markers the step forks: the correction loop runs on the
-// high-priority stream while collide+stream covers every row segment free of
-// band nodes on the main stream; after the join, collide+stream covers the
-// band segments, then moving bodies are advanced and re-binned.
+// launch.  With markers the step forks: the correction-loop kernel (which
+// ends with collide+stream of the band row segments) runs on the
+// high-priority stream while collide+stream covers every band-free row
+// segment on the main stream; after the join, moving bodies are advanced
+// and re-binned.
 void enqueue_step(Ctx& h, int parity, bool macro, bool timing) {
   const bool t = timing && h.ev_used < kEventPairs;
   cudaEvent_t* e = t ? &h.ev[kEventsPerStep * h.ev_used] : nullptr;
   if (h.nm == 0) {
     if (t) cudaEventRecord(e[0], h.stream);
     launch_collide_stream(h, parity, macro, K1_ALL, h.stream);
-    if (t) { cudaEventRecord(e[1], h.stream); cudaEventRecord(e[2], h.stream); cudaEventRecord(e[3], h.stream); }
+    if (t) cudaEventRecord(e[1], h.stream);
   } else {
     cudaEventRecord(h.ev_fork, h.stream);
     cudaStreamWaitEvent(h.ib_stream, h.ev_fork, 0);
-    launch_ib_loop(h, parity, h.ib_stream);
+    launch_ib_loop(h, parity, macro, h.ib_stream);
     cudaEventRecord(h.ev_join, h.ib_stream);
     if (t) cudaEventRecord(e[0], h.stream);
     launch_collide_stream(h, parity, macro, K1_MAIN, h.stream);
     if (t) cudaEventRecord(e[1], h.stream);
     cudaStreamWaitEvent(h.stream, h.ev_join, 0);
-    if (t) cudaEventRecord(e[2], h.stream);
-    launch_collide_stream(h, parity, macro, K1_BAND, h.stream);
-    if (t) cudaEventRecord(e[3], h.stream);
     launch_body_update(h, h.stream);
   }
   if (t) h.ev_used++;
@@ -141,11 +141,10 @@ ibm_status fold_events(Ctx* h) {
   if (h->ev_used == 0) return IBM_OK;
   IBM_CK(h, cudaStreamSynchronize(h->stream));
   for (int k = 0; k < h->ev_used; ++k) {
-    float a = 0.f, b = 0.f;
+    float a = 0.f;
     cudaEvent_t* e = &h->ev[kEventsPerStep * k];
     IBM_CK(h, cudaEventElapsedTime(&a, e[0], e[1]));
-    IBM_CK(h, cudaEventElapsedTime(&b, e[2], e[3]));
-    h->acc_ms += a + b;
+    h->acc_ms += a;
   }
   h->acc_n += h->ev_used;
   h->ev_used = 0;
@@ -157,8 +156,8 @@ ibm_status upload_markers(Ctx* h) {
   const int M = c.nm;
   // release the previous marker-sized buffers
   void* olds[] = {c.dX, c.dY, c.dds, c.ddX, c.ddY, c.dmbody, c.dUx, c.dUy, c.dW, c.dnode_of,
-                  c.dband_of, c.dclaim, c.dbnode, c.dbcnt, c.dent_m, c.dent_w, c.dbrho, c.dbJ0,
-                  c.dA0, c.dA1, c.dCm, c.dbodies};
+                  c.dband_of, c.dclaim, c.dbnode, c.dbcnt, c.dent, c.dbrho, c.dbJ0,
+                  c.dA0, c.dA1, c.dCm, c.dbodies, c.dfpart};
   IBM_CK(h, cudaStreamSynchronize(c.stream));
   // clear the node -> band map and segment flags of the old band
   IBM_CK(h, cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)c.geom.nx * c.geom.ny, c.stream));
@@ -185,8 +184,8 @@ ibm_status upload_markers(Ctx* h) {
   IBM_ALLOC(h, c.dclaim, int*, M * kStencil);
   IBM_ALLOC(h, c.dbnode, int*, c.bcap);
   IBM_ALLOC(h, c.dbcnt, int*, c.bcap);
-  IBM_ALLOC(h, c.dent_m, int*, (size_t)c.bcap * kBandCap);
-  c.dent_w = dev_alloc(c, R * (size_t)c.bcap * kBandCap);
+  c.dent = dev_alloc(c, (R == 8 ? sizeof(Ent<double>) : sizeof(Ent<float>)) * (size_t)c.bcap * kBandCap);
+  IBM_ALLOC(h, c.dfpart, double*, (size_t)c.ib_grid * c.nb * 3);
   c.dbrho = dev_alloc(c, R * c.bcap);
   c.dbJ0 = dev_alloc(c, R * 2 * c.bcap);
   c.dA0 = dev_alloc(c, R * 2 * M);
@@ -198,7 +197,7 @@ ibm_status upload_markers(Ctx* h) {
     c.segcap = (int)(c.bcap < nseg ? c.bcap : nseg);
     IBM_ALLOC(h, c.dseglist, int*, c.segcap);
   }
-  if (!c.dUx || !c.dUy || !c.dW || !c.dent_w || !c.dbrho || !c.dbJ0 || !c.dA0 || !c.dA1 || !c.dCm)
+  if (!c.dUx || !c.dUy || !c.dW || !c.dent || !c.dbrho || !c.dbJ0 || !c.dA0 || !c.dA1 || !c.dCm)
     return fail(h, IBM_ERR_NOMEM, "device allocation of marker arrays failed");
   IBM_CK(h, cudaMemcpyAsync(c.dX, c.hX.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
   IBM_CK(h, cudaMemcpyAsync(c.dY, c.hY.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
@@ -333,6 +332,15 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     c.ib_prio = hi;   // numerically lowest = highest priority
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
+    const int per_sm = ib_blocks_per_sm(d.prec);
+    if (sms <= 0 || per_sm < 1) {
+      cudaGetLastError();
+      c.err = "the correction-loop kernel cannot be resident on this device";
+      return bail(IBM_ERR_CUDA);
+    }
+    c.ib_grid = sms;
     if (cudaStreamCreateWithPriority(&c.ib_stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -347,9 +355,10 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
     c.macro = dev_alloc(c, c.r_bytes * 3 * (size_t)d.nx * d.ny);
     c.dnode2band = (int*)dev_alloc(c, sizeof(int) * (size_t)d.nx * d.ny);
     c.dctr = (int*)dev_alloc(c, CTR_COUNT * sizeof(int));
+    c.dbar = (unsigned*)dev_alloc(c, 2 * sizeof(unsigned));
     c.dsegflag = (int*)dev_alloc(c, sizeof(int) * (size_t)c.nseg_x * d.ny);
     c.dresid = dev_alloc(c, c.r_bytes * (d.n_corr + 1));
-    if (!c.f || !c.macro || !c.dnode2band || !c.dctr || !c.dresid || !c.dsegflag) {
+    if (!c.f || !c.macro || !c.dnode2band || !c.dctr || !c.dresid || !c.dsegflag || !c.dbar) {
       c.err = "device allocation of the lattice failed";
       st = IBM_ERR_NOMEM;
       break;
@@ -357,6 +366,7 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
     if (cudaMemsetAsync(c.f, 0, c.s_bytes * 9 * (size_t)c.geom.plane, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)d.nx * d.ny, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dctr, 0, CTR_COUNT * sizeof(int), c.stream) != cudaSuccess ||
+        cudaMemsetAsync(c.dbar, 0, 2 * sizeof(unsigned), c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dsegflag, 0, sizeof(int) * (size_t)c.nseg_x * d.ny, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dresid, 0, c.r_bytes * (d.n_corr + 1), c.stream) != cudaSuccess) {
       c.err = std::string("device memset failed: ") + cudaGetErrorString(cudaGetLastError());
@@ -655,13 +665,14 @@ ibm_status ibm_kernel_times(ibm_handle h, double* ms_total, int* launches) {
   return IBM_OK;
 }
 
-ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodies, int* band_nodes) {
+ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodies, int* band_nodes,
+                         int* band_segments) {
   if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
   DeviceGuard guard(h->device);
   if (nodes) *nodes = (long long)h->geom.nx * h->geom.ny;
   if (markers) *markers = h->nm;
   if (bodies) *bodies = h->nb;
-  if (band_nodes) {
+  if (band_nodes || band_segments) {
     int ctr[CTR_COUNT] = {0, 0, 0, 0};
     if (h->nm > 0 && !h->band_valid) {
       launch_band_build(*h, h->stream);
@@ -669,7 +680,8 @@ ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodi
     }
     IBM_CK(h, cudaMemcpyAsync(ctr, h->dctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
     IBM_CK(h, cudaStreamSynchronize(h->stream));
-    *band_nodes = h->nm > 0 ? ctr[CTR_NBAND] : 0;
+    if (band_nodes) *band_nodes = h->nm > 0 ? ctr[CTR_NBAND] : 0;
+    if (band_segments) *band_segments = h->nm > 0 ? ctr[CTR_NSEG] : 0;
   }
   return IBM_OK;
 }

@@ -23,6 +23,7 @@
 // order (lists sorted after the parallel build), and every reduction has a
 // fixed tree shape; no floating-point atomics.
 #include "ibm_internal.h"
+#include "ibm_k1.cuh"
 
 namespace ibm {
 
@@ -122,7 +123,7 @@ template <class R>
 __global__ void k_band_fill(int M, const int* __restrict__ node_of, const R* __restrict__ W,
                             const double* __restrict__ ds, const int* __restrict__ node2band,
                             int* __restrict__ band_of, int* __restrict__ bcnt,
-                            int* __restrict__ ent_m, R* __restrict__ ent_w, int* __restrict__ ctr) {
+                            Ent<R>* __restrict__ ent, int* __restrict__ ctr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= M * kStencil) return;
   const int n = node_of[t];
@@ -132,8 +133,10 @@ __global__ void k_band_fill(int M, const int* __restrict__ node_of, const R* __r
   const int l = t / kStencil;
   const int pos = atomicAdd(&bcnt[b], 1);
   if (pos < kBandCap) {
-    ent_m[(long long)b * kBandCap + pos] = l;
-    ent_w[(long long)b * kBandCap + pos] = (R)((double)W[t] * ds[l]);
+    Ent<R> e;
+    e.m = l;
+    e.w = (R)((double)W[t] * ds[l]);
+    ent[(long long)b * kBandCap + pos] = e;
   } else {
     atomicOr(&ctr[CTR_ERR], ERR_LIST_CAP);
   }
@@ -141,191 +144,319 @@ __global__ void k_band_fill(int M, const int* __restrict__ node_of, const R* __r
 
 template <class R>
 __global__ void k_band_sort(const int* __restrict__ ctr, int* __restrict__ bcnt,
-                            int* __restrict__ ent_m, R* __restrict__ ent_w, int bcap) {
+                            Ent<R>* __restrict__ ent, int bcap) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= min(ctr[CTR_NBAND], bcap)) return;
   const int n = min(bcnt[b], kBandCap);
   bcnt[b] = n;
-  int* m = ent_m + (long long)b * kBandCap;
-  R* w = ent_w + (long long)b * kBandCap;
+  Ent<R>* e = ent + (long long)b * kBandCap;
   for (int i = 1; i < n; ++i) {          // insertion sort by marker id
-    const int km = m[i];
-    const R kw = w[i];
+    const Ent<R> k = e[i];
     int j = i - 1;
-    while (j >= 0 && m[j] > km) { m[j + 1] = m[j]; w[j + 1] = w[j]; --j; }
-    m[j + 1] = km; w[j + 1] = kw;
+    while (j >= 0 && e[j].m > k.m) { e[j + 1] = e[j]; --j; }
+    e[j + 1] = k;
   }
 }
 
 // ------------------------------------------------------------------ IB loop
-// Gather (rho, j^0) at every band node from the post-stream populations.
+// One persistent kernel runs the whole correction loop of a step, one CTA
+// per SM, with a bounded grid barrier between the phases that need all
+// markers (Jacobi iterations).  Phases:
+//   gather  (rho, j^0) of every band node from the post-stream state;
+//   N iterations over the markers (16 lanes per marker, one per stencil
+//     node), each followed by a barrier;
+//   residual pass r^N, application of the summed correction to f on every
+//     band node, per-CTA partial sums of body force and torque; barrier;
+//   collide+stream of the band row segments (the rest of the lattice is
+//     handled concurrently by the band-free collide+stream launch), and the
+//     final force sums.
 template <int P>
-__global__ void k_ib_gather(Geom g, StepConsts<typename Prec<P>::R> c,
-                            const typename Prec<P>::S* __restrict__ A, int parity,
-                            const int* __restrict__ ctr, const int* __restrict__ bnode,
-                            typename Prec<P>::R* __restrict__ brho, typename Prec<P>::R* __restrict__ bJ,
-                            int bcap) {
+struct IbArgs {
+  typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= min(ctr[CTR_NBAND], bcap)) return;
-  const int n = bnode[b];
-  const int x = n % g.nx, y = n / g.nx;
-  R p[9], rho, jx, jy;
-  long long where;
+  Geom g;
+  StepConsts<R> c;
+  S* A;
+  R* mac;
+  int* ctr;
+  int bcap, M, N, nb, nseg_x;
+  const int* bnode;
+  R* brho;
+  R* bJ;
+  const int* bcnt;
+  const Ent<R>* ent;
+  const int* band_of;
+  const R* W;
+  R* A0;
+  R* A1;
+  R* Cm;
+  const R* Ux;
+  const R* Uy;
+  R* resid;
+  const int* seglist;
+  BodyDev* bodies;
+  const int* mbody;
+  const double* X;
+  const double* Y;
+  const double* ds;
+  double* fpart;              // [gridDim][nb][3]
+  unsigned* bar;              // [0] arrivals, [1] generation
+};
+
+// Grid barrier for a launch whose CTAs are all resident (one per SM).  The
+// wait is bounded: after kBarrierCycles the CTA records ERR_BARRIER and goes
+// on, so a broken launch ends with an error status instead of hanging.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        __nanosleep(64);
+        if (clock64() - t0 > kBarrierCycles) { atomicOr(&ctr[CTR_ERR], ERR_BARRIER); break; }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <class R>
+__device__ __forceinline__ R block_max(R v) {
+  __shared__ R red[kIbThreads / 32];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) p[i] = post_stream<P>(g, c, A, parity, x, y, i, where);
-  moments9<R>(p, rho, jx, jy);
-  brho[b] = rho;
-  bJ[2 * b] = jx;
-  bJ[2 * b + 1] = jy;
+  for (int off = 16; off >= 1; off >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R m = red[0];
+  for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
+  __syncthreads();
+  return m;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = kIbThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
 }
 
 // Current momentum of band node b: j^0 plus the spread of the accumulated
-// deviations A of the markers covering it, in ascending marker order.
+// deviations of the markers covering it, in ascending marker order.
 template <class R>
 __device__ __forceinline__ void band_momentum(int b, const R* __restrict__ bJ, const int* __restrict__ bcnt,
-                                              const int* __restrict__ ent_m, const R* __restrict__ ent_w,
-                                              const R* __restrict__ Acc, R& jx, R& jy) {
+                                              const Ent<R>* __restrict__ ent, const R* __restrict__ Acc,
+                                              R& jx, R& jy) {
   jx = bJ[2 * b];
   jy = bJ[2 * b + 1];
   const int n = bcnt[b];
-  const long long o = (long long)b * kBandCap;
-  for (int e = 0; e < n; ++e) {
-    const int m = ent_m[o + e];
-    const R w = ent_w[o + e];
-    jx += w * Acc[2 * m];
-    jy += w * Acc[2 * m + 1];
+  const Ent<R>* e = ent + (long long)b * kBandCap;
+  for (int k = 0; k < n; ++k) {
+    const Ent<R> q = e[k];
+    jx += q.w * Acc[2 * q.m];
+    jy += q.w * Acc[2 * q.m + 1];
   }
 }
 
-// One correction iteration (or, with UPDATE = false, the residual pass):
-// 16 lanes per marker, one per stencil node.  Each lane forms its node's
-// current rho, j, Pi = j j / rho, weighted by W; a 16-lane butterfly gives
-// (rho*, j*, Pi*) (Eq. 22b with Eq. 28 in moment form); lane 0 forms the
-// deviation, accumulates A and C, and the residual |j*/rho* - U|.
-template <class R, bool FIRST, bool UPDATE>
-__global__ void __launch_bounds__(256) k_ib_iterate(
-    int M, const int* __restrict__ band_of, const R* __restrict__ W, const R* __restrict__ brho,
-    const R* __restrict__ bJ, const int* __restrict__ bcnt, const int* __restrict__ ent_m,
-    const R* __restrict__ ent_w, const R* __restrict__ Ain, R* __restrict__ Aout, R* __restrict__ Cm,
-    const R* __restrict__ Ux, const R* __restrict__ Uy, R* __restrict__ resid) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int l = t / kStencil;
-  const bool valid = l < M;
-  const int b = valid ? band_of[t] : -1;
-  R w = R(0), rho = R(1), jx = R(0), jy = R(0);
-  if (b >= 0) {
-    w = W[t];
-    rho = brho[b];
-    if (FIRST) { jx = bJ[2 * b]; jy = bJ[2 * b + 1]; }
-    else band_momentum<R>(b, bJ, bcnt, ent_m, ent_w, Ain, jx, jy);
-  }
-  const R inv = R(1) / rho;
-  R v0 = w * rho, v1 = w * jx, v2 = w * jy;
-  R v3 = w * (jx * jx * inv), v4 = w * (jx * jy * inv), v5 = w * (jy * jy * inv);
+// One pass over all markers, two markers per warp: each lane forms its
+// stencil node's weighted rho, j, Pi = j j / rho; a 16-lane butterfly gives
+// (rho*, j*, Pi*) (Eq. 22b with Eq. 28 in moment form); lane 0 of the marker
+// forms the residual |j*/rho* - U| and, when updating, the deviation
+// (dj, dPi) added to A (Jacobi: read Ain, write Aout) and C.  Returns the
+// largest residual seen by this thread.
+template <class R>
+__device__ R marker_pass_impl(const int M, const int* __restrict__ band_of, const R* __restrict__ W,
+                              const R* __restrict__ brho, const R* __restrict__ bJ,
+                              const int* __restrict__ bcnt, const Ent<R>* __restrict__ ent,
+                              const R* __restrict__ Ain, R* __restrict__ Aout, R* __restrict__ Cm,
+                              const R* __restrict__ Ux, const R* __restrict__ Uy, bool first, bool update) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  R rmax = R(0);
+  for (int base = 2 * warp; base < M; base += 2 * nwarp) {
+    const int l = base + (lane >> 4);
+    const bool valid = l < M;
+    const int t = l * kStencil + (lane & 15);
+    const int b = valid ? band_of[t] : -1;
+    R w = R(0), rho = R(1), jx = R(0), jy = R(0);
+    if (b >= 0) {
+      w = W[t];
+      rho = brho[b];
+      if (first) { jx = bJ[2 * b]; jy = bJ[2 * b + 1]; }
+      else band_momentum<R>(b, bJ, bcnt, ent, Ain, jx, jy);
+    }
+    const R inv = R(1) / rho;
+    R v0 = w * rho, v1 = w * jx, v2 = w * jy;
+    R v3 = w * (jx * jx * inv), v4 = w * (jx * jy * inv), v5 = w * (jy * jy * inv);
 #pragma unroll
-  for (int off = kStencil / 2; off >= 1; off >>= 1) {
-    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-    v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-    v3 += __shfl_xor_sync(0xffffffffu, v3, off);
-    v4 += __shfl_xor_sync(0xffffffffu, v4, off);
-    v5 += __shfl_xor_sync(0xffffffffu, v5, off);
-  }
-  R r = R(0);
-  if (valid && (t % kStencil) == 0) {
-    const R ux = Ux[l], uy = Uy[l];
-    const R rs = v0;
-    const R ex = v1 / rs - ux, ey = v2 / rs - uy;
-    r = sqrt(ex * ex + ey * ey);
-    if (UPDATE) {
-      const R djx = rs * ux - v1, djy = rs * uy - v2;
-      const R dpxx = rs * ux * ux - v3, dpxy = rs * ux * uy - v4, dpyy = rs * uy * uy - v5;
-      if (FIRST) {
-        Aout[2 * l] = djx; Aout[2 * l + 1] = djy;
-        Cm[3 * l] = dpxx; Cm[3 * l + 1] = dpxy; Cm[3 * l + 2] = dpyy;
-      } else {
-        Aout[2 * l] = Ain[2 * l] + djx; Aout[2 * l + 1] = Ain[2 * l + 1] + djy;
-        Cm[3 * l] += dpxx; Cm[3 * l + 1] += dpxy; Cm[3 * l + 2] += dpyy;
+    for (int off = kStencil / 2; off >= 1; off >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+      v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+      v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+      v4 += __shfl_xor_sync(0xffffffffu, v4, off);
+      v5 += __shfl_xor_sync(0xffffffffu, v5, off);
+    }
+    if (valid && (lane & 15) == 0) {
+      const R ux = Ux[l], uy = Uy[l];
+      const R rs = v0;
+      const R ex = v1 / rs - ux, ey = v2 / rs - uy;
+      rmax = nanmax(rmax, (R)sqrt(ex * ex + ey * ey));
+      if (update) {
+        const R djx = rs * ux - v1, djy = rs * uy - v2;
+        const R dpxx = rs * ux * ux - v3, dpxy = rs * ux * uy - v4, dpyy = rs * uy * uy - v5;
+        if (first) {
+          Aout[2 * l] = djx; Aout[2 * l + 1] = djy;
+          Cm[3 * l] = dpxx; Cm[3 * l + 1] = dpxy; Cm[3 * l + 2] = dpyy;
+        } else {
+          Aout[2 * l] = Ain[2 * l] + djx; Aout[2 * l + 1] = Ain[2 * l + 1] + djy;
+          Cm[3 * l] += dpxx; Cm[3 * l + 1] += dpxy; Cm[3 * l + 2] += dpyy;
+        }
       }
     }
   }
-  // block max of the residual, one atomic per block
-  __shared__ R red[256 / 32];
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) r = nanmax(r, __shfl_xor_sync(0xffffffffu, r, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R m = red[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = nanmax(m, red[k]);
-    if (m > R(0) || m != m) AtomicBits<R>::max(resid, m);
-  }
+  return rmax;
 }
 
-// Apply the summed correction of all iterations at every band node (Eq. 27
-// summed over n): f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi].
-template <int P>
-__global__ void k_ib_apply(Geom g, StepConsts<typename Prec<P>::R> c, typename Prec<P>::S* __restrict__ A,
-                           int parity, const int* __restrict__ ctr, const int* __restrict__ bnode,
-                           const int* __restrict__ bcnt, const int* __restrict__ ent_m,
-                           const typename Prec<P>::R* __restrict__ ent_w,
-                           const typename Prec<P>::R* __restrict__ Acc,
-                           const typename Prec<P>::R* __restrict__ Cm, int bcap) {
+template <int P, int PAR, bool MACRO>
+__global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
   typedef typename Prec<P>::R R;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= min(ctr[CTR_NBAND], bcap)) return;
-  R jx = R(0), jy = R(0), pxx = R(0), pxy = R(0), pyy = R(0);
-  const int cnt = bcnt[b];
-  const long long o = (long long)b * kBandCap;
-  for (int e = 0; e < cnt; ++e) {
-    const int m = ent_m[o + e];
-    const R w = ent_w[o + e];
-    jx += w * Acc[2 * m];
-    jy += w * Acc[2 * m + 1];
-    pxx += w * Cm[3 * m];
-    pxy += w * Cm[3 * m + 1];
-    pyy += w * Cm[3 * m + 2];
-  }
-  const int n = bnode[b];
-  const int x = n % g.nx, y = n / g.nx;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const int nband = min(a.ctr[CTR_NBAND], a.bcap);
+  long long where;
+
+  // gather (rho, j^0) at every band node
+  for (int b = tid; b < nband; b += nth) {
+    const int n = a.bnode[b];
+    const int x = n % a.g.nx, y = n / a.g.nx;
+    R p[9], rho, jx, jy;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    long long where;
-    post_stream<P>(g, c, A, parity, x, y, i, where);
-    if (where < 0) continue;
-    const int slot = (int)(where / g.plane);
-    const R df = feq_i<R>(i, R(0), jx, jy, pxx, pxy, pyy);
-    A[where] = Prec<P>::st(Prec<P>::ld(A[where], slot) + df, slot);
+    for (int i = 0; i < 9; ++i) p[i] = post_stream<P>(a.g, a.c, a.A, PAR, x, y, i, where);
+    moments9<R>(p, rho, jx, jy);
+    a.brho[b] = rho;
+    a.bJ[2 * b] = jx;
+    a.bJ[2 * b + 1] = jy;
+  }
+  grid_barrier(a.bar, a.ctr);
+
+  // correction iterations (Eqs. 22-27), Jacobi over markers
+  R* acc[2] = {a.A0, a.A1};
+  for (int n = 0; n < a.N; ++n) {
+    const R r = marker_pass_impl<R>(a.M, a.band_of, a.W, a.brho, a.bJ, a.bcnt, a.ent, acc[n & 1],
+                                    acc[(n + 1) & 1], a.Cm, a.Ux, a.Uy, n == 0, true);
+    const R m = block_max<R>(r);
+    if (threadIdx.x == 0 && (m > R(0) || m != m)) AtomicBits<R>::max(a.resid + n, m);
+    grid_barrier(a.bar, a.ctr);
+  }
+  const R* afin = acc[a.N & 1];
+
+  // final residual r^N (no correction)
+  {
+    const R r = marker_pass_impl<R>(a.M, a.band_of, a.W, a.brho, a.bJ, a.bcnt, a.ent, afin, nullptr,
+                                    nullptr, a.Ux, a.Uy, a.N == 0, false);
+    const R m = block_max<R>(r);
+    if (threadIdx.x == 0 && (m > R(0) || m != m)) AtomicBits<R>::max(a.resid + a.N, m);
+  }
+
+  // Eq. 27 summed over the iterations: f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi]
+  if (a.N > 0) {
+    for (int b = tid; b < nband; b += nth) {
+      R jx = R(0), jy = R(0), pxx = R(0), pxy = R(0), pyy = R(0);
+      const int cnt = a.bcnt[b];
+      const Ent<R>* e = a.ent + (long long)b * kBandCap;
+      for (int k = 0; k < cnt; ++k) {
+        const Ent<R> q = e[k];
+        jx += q.w * afin[2 * q.m];
+        jy += q.w * afin[2 * q.m + 1];
+        pxx += q.w * a.Cm[3 * q.m];
+        pxy += q.w * a.Cm[3 * q.m + 1];
+        pyy += q.w * a.Cm[3 * q.m + 2];
+      }
+      const int n = a.bnode[b];
+      const int x = n % a.g.nx, y = n / a.g.nx;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        post_stream<P>(a.g, a.c, a.A, PAR, x, y, i, where);
+        if (where < 0) continue;
+        const int slot = (int)(where / a.g.plane);
+        const R df = feq_i<R>(i, R(0), jx, jy, pxx, pxy, pyy);
+        a.A[where] = Prec<P>::st(Prec<P>::ld(a.A[where], slot) + df, slot);
+      }
+    }
+  }
+
+  // Eq. 29: per-CTA partial force and torque of each body over a fixed
+  // chunk of markers, F_l = -ds_l A_l, T_l = (X_l - x_c) x F_l (FP64).
+  __shared__ double sh[kIbThreads];
+  const int chunk = (a.M + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(a.M, lo + chunk);
+  if (a.nb > 0 && lo < hi) {
+    const int b0 = a.mbody[lo], b1 = a.mbody[hi - 1];
+    for (int bd = b0; bd <= b1; ++bd) {
+      const BodyDev& B = a.bodies[bd];
+      const int l0 = max(lo, B.m0), l1 = min(hi, B.m1);
+      double fx = 0.0, fy = 0.0, tq = 0.0;
+      for (int l = l0 + (int)threadIdx.x; l < l1; l += blockDim.x) {
+        const double Fx = -a.ds[l] * (double)afin[2 * l], Fy = -a.ds[l] * (double)afin[2 * l + 1];
+        fx += Fx;
+        fy += Fy;
+        tq += (a.X[l] - B.xc[0]) * Fy - (a.Y[l] - B.xc[1]) * Fx;
+      }
+      fx = block_sum(fx, sh);
+      fy = block_sum(fy, sh);
+      tq = block_sum(tq, sh);
+      if (threadIdx.x == 0) {
+        double* o = a.fpart + ((long long)blockIdx.x * a.nb + bd) * 3;
+        o[0] = fx; o[1] = fy; o[2] = tq;
+      }
+    }
+  }
+  grid_barrier(a.bar, a.ctr);
+
+  // collide+stream of the band row segments
+  {
+    const int nseg = a.ctr[CTR_NSEG];
+    const int lane = threadIdx.x & (kSegW - 1);
+    for (int k = tid / kSegW; k < nseg; k += nth / kSegW) {
+      const int seg = a.seglist[k];
+      const int y = seg / a.nseg_x, x = (seg % a.nseg_x) * kSegW + lane;
+      if (x >= a.g.nx) continue;
+      if (PAR == 0) even_node<P, MACRO>(a.g, a.c, a.A, a.mac, x, y);
+      else odd_node<P, MACRO>(a.g, a.c, a.A, a.mac, x, y);
+    }
+  }
+
+  // body totals in fixed order over the CTA chunks
+  if (blockIdx.x == 0) {
+    for (int bd = threadIdx.x; bd < a.nb; bd += blockDim.x) {
+      BodyDev& B = a.bodies[bd];
+      const int k0 = B.m0 / chunk, k1 = (B.m1 - 1) / chunk;
+      double f[3] = {0.0, 0.0, 0.0};
+      for (int k = k0; k <= k1; ++k)
+        for (int q = 0; q < 3; ++q) f[q] += a.fpart[((long long)k * a.nb + bd) * 3 + q];
+      B.F_ib[0] = f[0];
+      B.F_ib[1] = f[1];
+      B.T_ib = f[2];
+    }
   }
 }
 
 // ------------------------------------------------------------------ bodies
-// Eq. 29 per body in FP64 with a fixed-shape block reduction:
-// F = -sum_l ds_l A_l,  T = sum_l (X_l - x_c) x F_l.
-template <class R>
-__global__ void __launch_bounds__(256) k_body_force(BodyDev* __restrict__ bodies,
-                                                   const double* __restrict__ X, const double* __restrict__ Y,
-                                                   const double* __restrict__ ds, const R* __restrict__ Acc) {
-  BodyDev& B = bodies[blockIdx.x];
-  double fx = 0.0, fy = 0.0, tq = 0.0;
-  for (int l = B.m0 + threadIdx.x; l < B.m1; l += blockDim.x) {
-    const double Fx = -ds[l] * (double)Acc[2 * l], Fy = -ds[l] * (double)Acc[2 * l + 1];
-    fx += Fx;
-    fy += Fy;
-    tq += (X[l] - B.xc[0]) * Fy - (Y[l] - B.xc[1]) * Fx;
-  }
-  __shared__ double s[3][256];
-  s[0][threadIdx.x] = fx; s[1][threadIdx.x] = fy; s[2][threadIdx.x] = tq;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h)
-      for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) { B.F_ib[0] = s[0][0]; B.F_ib[1] = s[1][0]; B.T_ib = s[2][0]; }
-}
-
 // Eq. 39 on body i from a partner at offset d = x_i - x_j.
 __device__ void collision_force(const BodyDev& Bi, double Rj, double dx, double dy, double* F) {
   const double eps_c = 0.01, xi = 0.05 * 2.0 * Bi.radius;
@@ -421,8 +552,8 @@ static void band_build_t(const Ctx& h, cudaStream_t s) {
   k_band_alloc<<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, h.dclaim, h.dnode2band, h.dbnode,
                                                   h.dbcnt, h.dctr, h.bcap);
   k_band_fill<R><<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, (const R*)h.dW, h.dds, h.dnode2band,
-                                                     h.dband_of, h.dbcnt, h.dent_m, (R*)h.dent_w, h.dctr);
-  k_band_sort<R><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.dctr, h.dbcnt, h.dent_m, (R*)h.dent_w, h.bcap);
+                                                     h.dband_of, h.dbcnt, (Ent<R>*)h.dent, h.dctr);
+  k_band_sort<R><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.dctr, h.dbcnt, (Ent<R>*)h.dent, h.bcap);
   k_band_segments<<<blocks_for(h.bcap, 256), 256, 0, s>>>(h.geom, h.dbnode, h.dsegflag, h.dseglist, h.dctr,
                                                           h.nseg_x, h.bcap, h.segcap);
 }
@@ -433,62 +564,78 @@ void launch_band_build(const Ctx& h, cudaStream_t s) {
 }
 
 template <int P>
-static void ib_loop_t(const Ctx& h, int parity, cudaStream_t s) {
+static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
   if (h.nm == 0) return;
-  const int N = h.desc.n_corr;
-  const int pr = h.ib_prio;
-  StepConsts<R> c = make_consts<R>(h);
-  S* A = (S*)h.f;
-  cudaMemsetAsync(h.dresid, 0, sizeof(R) * (N + 1), s);
-  launch_prio(k_ib_gather<P>, dim3(blocks_for(h.bcap, 128)), dim3(128), s, pr, h.geom, c, (const S*)A,
-              parity, (const int*)h.dctr, (const int*)h.dbnode, (R*)h.dbrho, (R*)h.dbJ0, h.bcap);
-  const dim3 gridM(blocks_for((long long)h.nm * kStencil, 256));
-  R* Acc[2] = {(R*)h.dA0, (R*)h.dA1};
-  R* resid = (R*)h.dresid;
-  const int* band_of = h.dband_of;
-  const R* W = (const R*)h.dW;
-  const R* brho = (const R*)h.dbrho;
-  const R* bJ = (const R*)h.dbJ0;
-  const int* bcnt = h.dbcnt;
-  const int* ent_m = h.dent_m;
-  const R* ent_w = (const R*)h.dent_w;
-  const R* Ux = (const R*)h.dUx;
-  const R* Uy = (const R*)h.dUy;
-  R* Cm = (R*)h.dCm;
-  for (int n = 0; n < N; ++n) {
-    const R* ain = Acc[n & 1];
-    R* aout = Acc[(n + 1) & 1];
-    if (n == 0)
-      launch_prio(k_ib_iterate<R, true, true>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
-                  ent_m, ent_w, ain, aout, Cm, Ux, Uy, resid + n);
-    else
-      launch_prio(k_ib_iterate<R, false, true>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
-                  ent_m, ent_w, ain, aout, Cm, Ux, Uy, resid + n);
+  IbArgs<P> a;
+  a.g = h.geom;
+  a.c = make_consts<R>(h);
+  a.A = (S*)h.f;
+  a.mac = (R*)h.macro;
+  a.ctr = h.dctr;
+  a.bcap = h.bcap;
+  a.M = h.nm;
+  a.N = h.desc.n_corr;
+  a.nb = h.nb;
+  a.nseg_x = h.nseg_x;
+  a.bnode = h.dbnode;
+  a.brho = (R*)h.dbrho;
+  a.bJ = (R*)h.dbJ0;
+  a.bcnt = h.dbcnt;
+  a.ent = (const Ent<R>*)h.dent;
+  a.band_of = h.dband_of;
+  a.W = (const R*)h.dW;
+  a.A0 = (R*)h.dA0;
+  a.A1 = (R*)h.dA1;
+  a.Cm = (R*)h.dCm;
+  a.Ux = (const R*)h.dUx;
+  a.Uy = (const R*)h.dUy;
+  a.resid = (R*)h.dresid;
+  a.seglist = h.dseglist;
+  a.bodies = h.dbodies;
+  a.mbody = h.dmbody;
+  a.X = h.dX;
+  a.Y = h.dY;
+  a.ds = h.dds;
+  a.fpart = h.dfpart;
+  a.bar = h.dbar;
+  cudaMemsetAsync(h.dresid, 0, sizeof(R) * (a.N + 1), s);
+  const dim3 grid(h.ib_grid), block(kIbThreads);
+  if (parity == 0) {
+    if (macro) launch_prio(k_ib_step<P, 0, true>, grid, block, s, h.ib_prio, a);
+    else launch_prio(k_ib_step<P, 0, false>, grid, block, s, h.ib_prio, a);
+  } else {
+    if (macro) launch_prio(k_ib_step<P, 1, true>, grid, block, s, h.ib_prio, a);
+    else launch_prio(k_ib_step<P, 1, false>, grid, block, s, h.ib_prio, a);
   }
-  const R* afin = Acc[N & 1];
-  R* none = nullptr;
-  if (N == 0)
-    launch_prio(k_ib_iterate<R, true, false>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
-                ent_m, ent_w, afin, none, none, Ux, Uy, resid + N);
-  else
-    launch_prio(k_ib_iterate<R, false, false>, gridM, dim3(256), s, pr, h.nm, band_of, W, brho, bJ, bcnt,
-                ent_m, ent_w, afin, none, none, Ux, Uy, resid + N);
-  if (N > 0)
-    launch_prio(k_ib_apply<P>, dim3(blocks_for(h.bcap, 128)), dim3(128), s, pr, h.geom, c, A, parity,
-                (const int*)h.dctr, (const int*)h.dbnode, bcnt, ent_m, ent_w, afin, (const R*)Cm, h.bcap);
-  if (h.nb > 0)
-    launch_prio(k_body_force<R>, dim3(h.nb), dim3(256), s, pr, h.dbodies, (const double*)h.dX,
-                (const double*)h.dY, (const double*)h.dds, afin);
 }
 
-void launch_ib_loop(const Ctx& h, int parity, cudaStream_t s) {
+void launch_ib_loop(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   switch (h.prec) {
-    case PREC_FP64: ib_loop_t<PREC_FP64>(h, parity, s); break;
-    case PREC_FP32: ib_loop_t<PREC_FP32>(h, parity, s); break;
-    case PREC_FP16_DEV: ib_loop_t<PREC_FP16_DEV>(h, parity, s); break;
-    default: ib_loop_t<PREC_BF16_DEV>(h, parity, s); break;
+    case PREC_FP64: ib_loop_t<PREC_FP64>(h, parity, macro, s); break;
+    case PREC_FP32: ib_loop_t<PREC_FP32>(h, parity, macro, s); break;
+    case PREC_FP16_DEV: ib_loop_t<PREC_FP16_DEV>(h, parity, macro, s); break;
+    default: ib_loop_t<PREC_BF16_DEV>(h, parity, macro, s); break;
+  }
+}
+
+// Largest co-resident CTA count of the correction-loop kernel (1 per SM is
+// used; the kernel's grid barrier needs every CTA resident).
+template <int P>
+static int ib_blocks_per_sm_t() {
+  int n0 = 0, n1 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ib_step<P, 0, true>, kIbThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ib_step<P, 1, true>, kIbThreads, 0);
+  return n0 < n1 ? n0 : n1;
+}
+
+int ib_blocks_per_sm(int prec) {
+  switch (prec) {
+    case PREC_FP64: return ib_blocks_per_sm_t<PREC_FP64>();
+    case PREC_FP32: return ib_blocks_per_sm_t<PREC_FP32>();
+    case PREC_FP16_DEV: return ib_blocks_per_sm_t<PREC_FP16_DEV>();
+    default: return ib_blocks_per_sm_t<PREC_BF16_DEV>();
   }
 }
 

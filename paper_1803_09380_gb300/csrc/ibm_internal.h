@@ -22,7 +22,18 @@ struct BodyDev {
   double F_ib[2], T_ib;     // Eq. 29 sums of the last step (no internal-mass terms)
 };
 
-enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4 };
+enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4, ERR_BARRIER = 8 };
+
+// One entry of a band node's list of covering markers: marker id and its
+// spreading weight W_l(x) ds_l.
+template <class R>
+struct Ent {
+  int m;
+  R w;
+};
+
+constexpr int kIbThreads = 256;                  // threads per correction-loop CTA
+constexpr long long kBarrierCycles = 4000000000LL; // ~2 s at 2 GHz: grid-barrier wait limit
 
 // Device counters: band nodes, band row segments, error bits.
 enum { CTR_NBAND = 0, CTR_NSEG = 1, CTR_ERR = 2, CTR_COUNT = 4 };
@@ -30,7 +41,7 @@ enum { CTR_NBAND = 0, CTR_NSEG = 1, CTR_ERR = 2, CTR_COUNT = 4 };
 // Collide+stream launch modes: every node; every 32-node row segment
 // without a band node (runs while the correction loop runs); the band
 // segments only (after the correction).
-enum { K1_ALL = 0, K1_MAIN = 1, K1_BAND = 2 };
+enum { K1_ALL = 0, K1_MAIN = 1 };
 constexpr int kSegW = 32;
 
 enum {
@@ -77,8 +88,7 @@ struct Ctx {
   int* dnode2band = nullptr;                 // [ny nx] band index or -1
   int* dbnode = nullptr;                     // [bcap] node of band entry
   int* dbcnt = nullptr;                      // [bcap] covering markers
-  int* dent_m = nullptr;                     // [bcap * kBandCap] marker ids (ascending)
-  void* dent_w = nullptr;                    // [bcap * kBandCap] W ds (R)
+  void* dent = nullptr;                      // [bcap * kBandCap] Ent<R>, ascending marker id
   void *dbrho = nullptr, *dbJ0 = nullptr;    // [bcap], [2 bcap] (R)
   void *dA0 = nullptr, *dA1 = nullptr;       // [2 nm] accumulated momentum deviation (R)
   void* dCm = nullptr;                       // [3 nm] accumulated second-moment deviation (R)
@@ -89,6 +99,9 @@ struct Ctx {
   int* dsegflag = nullptr;                   // [ny][nseg_x] 1 if the segment has a band node
   int* dseglist = nullptr;                   // [segcap] band segments
   BodyDev* dbodies = nullptr;
+  double* dfpart = nullptr;                  // [ib_grid][nb][3] force partial sums
+  unsigned* dbar = nullptr;                  // grid barrier state of the correction kernel
+  int ib_grid = 0;                           // CTAs of the correction kernel (one per SM)
   bool band_valid = false;
 
   // CUDA graphs of one step, per parity and macro flag
@@ -117,9 +130,8 @@ inline int kernels_per_step(const Ctx& h) {
   int k = 1;                                       // collide + stream
   if (h.nm > 0) {
     const int N = h.desc.n_corr;
-    k += 1;                                        // collide + stream of the band segments
-    k += 1 + N + 1 + (N > 0 ? 1 : 0);              // gather, iterations, residual, apply
-    if (h.nb > 0) k += 1;                          // body force / torque
+    (void)N;
+    k += 1;                                        // correction loop (+ band collide+stream)
     if (h.nb > 0 && h.any_moving) k += 2 + 6;      // body update, marker move, band rebuild
   }
   return k;
@@ -169,7 +181,8 @@ void launch_fields(const Ctx& h, int op, const double* dev_in, double* dev_out, 
 
 // ibm_ib.cu
 void launch_band_build(const Ctx& h, cudaStream_t s);
-void launch_ib_loop(const Ctx& h, int parity, cudaStream_t s);
+void launch_ib_loop(const Ctx& h, int parity, bool macro, cudaStream_t s);
+int ib_blocks_per_sm(int prec);
 void launch_body_update(const Ctx& h, cudaStream_t s);
 
 }  // namespace ibm

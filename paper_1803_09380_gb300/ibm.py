@@ -96,7 +96,7 @@ def load(build_if_missing: bool = True):
         lib.ibm_sync.argtypes = [vp]
         lib.ibm_kernel_times.argtypes = [vp, _D, ctypes.POINTER(ci)]
         lib.ibm_get_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ci),
-                                      ctypes.POINTER(ci), ctypes.POINTER(ci)]
+                                      ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
         lib.ibm_get_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_longlong)]
         lib.ibm_destroy.argtypes = [vp]
@@ -209,11 +209,12 @@ def ibm_step(h, nsteps: int, flags: int = STEP_DEFAULT) -> None:
 
 
 def ibm_get_sizes(h):
-    """(nodes, markers, bodies, band_nodes)."""
-    n, m, b, bn = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(load().ibm_get_sizes(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(b), ctypes.byref(bn)),
-           h, "ibm_get_sizes")
-    return n.value, m.value, b.value, bn.value
+    """(nodes, markers, bodies, band_nodes, band_segments)."""
+    n, m, b, bn, bs = (ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(),
+                       ctypes.c_int())
+    _check(load().ibm_get_sizes(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(b),
+                                ctypes.byref(bn), ctypes.byref(bs)), h, "ibm_get_sizes")
+    return n.value, m.value, b.value, bn.value, bs.value
 
 
 def _field_shape(h, field, nx, ny, n_corr):
@@ -223,7 +224,7 @@ def _field_shape(h, field, nx, ny, n_corr):
         return (9, ny, nx)
     if field == FIELD_RESIDUAL:
         return (n_corr + 1,)
-    _, m, b, _ = ibm_get_sizes(h)
+    _, m, b, _, _ = ibm_get_sizes(h)
     if field == FIELD_BODIES:
         return (b, 9)
     if field == FIELD_MARKERS:

@@ -278,4 +278,4 @@ def test_zero_steps_and_empty_lattice():
     gpu.step(5)
     rho, ux, uy = gpu.moments()
     assert np.allclose(rho, 1.0) and np.all(ux == 0)
-    assert gpu.sizes() == (64, 0, 0, 0)
+    assert gpu.sizes() == (64, 0, 0, 0, 0)
