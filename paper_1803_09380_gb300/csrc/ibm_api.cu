@@ -91,6 +91,8 @@ ibm_status check_device_flags(Ctx* h) {
   if (ctr[CTR_ERR] & ERR_LIST_CAP)
     return fail(h, IBM_ERR_BOUNDS, "more than 32 markers cover one node (markers too dense)");
   if (ctr[CTR_ERR] & ERR_SEG_CAP) return fail(h, IBM_ERR_BOUNDS, "band segment capacity exceeded");
+  if (ctr[CTR_ERR] & ERR_G_CAP)
+    return fail(h, IBM_ERR_BOUNDS, "a marker couples to more than 64 markers (markers too dense)");
   if (ctr[CTR_ERR] & ERR_BARRIER)
     return fail(h, IBM_ERR_TIMEOUT, "the correction-loop grid barrier timed out");
   return IBM_OK;
@@ -156,8 +158,8 @@ ibm_status upload_markers(Ctx* h) {
   const int M = c.nm;
   // release the previous marker-sized buffers
   void* olds[] = {c.dX, c.dY, c.dds, c.ddX, c.ddY, c.dmbody, c.dUx, c.dUy, c.dW, c.dnode_of,
-                  c.dband_of, c.dclaim, c.dbnode, c.dbcnt, c.dent, c.dbrho, c.dbJ0,
-                  c.dA0, c.dA1, c.dCm, c.dbodies, c.dfpart};
+                  c.dband_of, c.dclaim, c.dbnode, c.dbcnt, c.dent, c.dbq, c.dmq, c.dAh,
+                  c.dCm, c.dG, c.dgcnt, c.dbodies, c.dfpart};
   IBM_CK(h, cudaStreamSynchronize(c.stream));
   // clear the node -> band map and segment flags of the old band
   IBM_CK(h, cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)c.geom.nx * c.geom.ny, c.stream));
@@ -186,18 +188,19 @@ ibm_status upload_markers(Ctx* h) {
   IBM_ALLOC(h, c.dbcnt, int*, c.bcap);
   c.dent = dev_alloc(c, (R == 8 ? sizeof(Ent<double>) : sizeof(Ent<float>)) * (size_t)c.bcap * kBandCap);
   IBM_ALLOC(h, c.dfpart, double*, (size_t)c.ib_grid * c.nb * 3);
-  c.dbrho = dev_alloc(c, R * c.bcap);
-  c.dbJ0 = dev_alloc(c, R * 2 * c.bcap);
-  c.dA0 = dev_alloc(c, R * 2 * M);
-  c.dA1 = dev_alloc(c, R * 2 * M);
-  c.dCm = dev_alloc(c, R * 3 * M);
+  c.dbq = dev_alloc(c, R * 8 * (size_t)c.bcap);
+  c.dmq = dev_alloc(c, R * 4 * (size_t)M);
+  c.dAh = dev_alloc(c, R * 2 * (size_t)M * (c.desc.n_corr + 1));
+  c.dCm = dev_alloc(c, R * 3 * (size_t)M);
+  c.dG = dev_alloc(c, (R == 8 ? sizeof(Ent<double>) : sizeof(Ent<float>)) * (size_t)M * kGCap);
+  IBM_ALLOC(h, c.dgcnt, int*, M);
   IBM_ALLOC(h, c.dbodies, BodyDev*, c.nb);
   {
     const long long nseg = (long long)c.nseg_x * c.geom.ny;
     c.segcap = (int)(c.bcap < nseg ? c.bcap : nseg);
     IBM_ALLOC(h, c.dseglist, int*, c.segcap);
   }
-  if (!c.dUx || !c.dUy || !c.dW || !c.dent || !c.dbrho || !c.dbJ0 || !c.dA0 || !c.dA1 || !c.dCm)
+  if (!c.dUx || !c.dUy || !c.dW || !c.dent || !c.dbq || !c.dmq || !c.dAh || !c.dCm || !c.dG)
     return fail(h, IBM_ERR_NOMEM, "device allocation of marker arrays failed");
   IBM_CK(h, cudaMemcpyAsync(c.dX, c.hX.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
   IBM_CK(h, cudaMemcpyAsync(c.dY, c.hY.data(), 8 * M, cudaMemcpyHostToDevice, c.stream));
@@ -214,9 +217,8 @@ ibm_status upload_markers(Ctx* h) {
   IBM_CK(h, cudaMemcpyAsync(c.dUy, uy.data(), R * M, cudaMemcpyHostToDevice, c.stream));
   IBM_CK(h, cudaMemcpyAsync(c.dbodies, c.hbodies.data(), sizeof(BodyDev) * c.nb,
                             cudaMemcpyHostToDevice, c.stream));
-  IBM_CK(h, cudaMemsetAsync(c.dA0, 0, R * 2 * M, c.stream));
-  IBM_CK(h, cudaMemsetAsync(c.dA1, 0, R * 2 * M, c.stream));
-  IBM_CK(h, cudaMemsetAsync(c.dCm, 0, R * 3 * M, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dAh, 0, R * 2 * (size_t)M * (c.desc.n_corr + 1), c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dCm, 0, R * 3 * (size_t)M, c.stream));
   IBM_CK(h, cudaMemsetAsync(c.dbcnt, 0, sizeof(int) * c.bcap, c.stream));
   IBM_CK(h, cudaStreamSynchronize(c.stream));   // host vectors are temporaries
   c.band_valid = false;

@@ -158,18 +158,72 @@ __global__ void k_band_sort(const int* __restrict__ ctr, int* __restrict__ bcnt,
   }
 }
 
+// ------------------------------------------------------------------ G matrix
+// Marker coupling of one spread followed by one interpolation:
+//   G_lm = sum_x W_l(x) W_m(x) ds_m,
+// summed over the shared stencil nodes x in stencil order, then stored by
+// ascending m.  One thread per marker.
+template <class R>
+__global__ void k_build_g(int M, const int* __restrict__ band_of, const R* __restrict__ W,
+                          const int* __restrict__ bcnt, const Ent<R>* __restrict__ ent,
+                          Ent<R>* __restrict__ G, int* __restrict__ gcnt, int* __restrict__ ctr) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= M) return;
+  int nm[kGCap];
+  R gv[kGCap];
+  int n = 0;
+  bool overflow = false;
+  for (int s = 0; s < kStencil; ++s) {
+    const int b = band_of[l * kStencil + s];
+    if (b < 0) continue;
+    const R wl = W[l * kStencil + s];
+    const Ent<R>* e = ent + (long long)b * kBandCap;
+    const int c = bcnt[b];
+    for (int k = 0; k < c; ++k) {
+      const Ent<R> q = e[k];
+      const R v = wl * q.w;
+      int j = 0;
+      while (j < n && nm[j] != q.m) ++j;
+      if (j < n) gv[j] += v;
+      else if (n < kGCap) { nm[n] = q.m; gv[n] = v; ++n; }
+      else overflow = true;
+    }
+  }
+  for (int i = 1; i < n; ++i) {          // ascending marker id
+    const int km = nm[i];
+    const R kv = gv[i];
+    int j = i - 1;
+    while (j >= 0 && nm[j] > km) { nm[j + 1] = nm[j]; gv[j + 1] = gv[j]; --j; }
+    nm[j + 1] = km; gv[j + 1] = kv;
+  }
+  for (int j = 0; j < n; ++j) {
+    Ent<R> q;
+    q.m = nm[j];
+    q.w = gv[j];
+    G[(long long)l * kGCap + j] = q;
+  }
+  gcnt[l] = n;
+  if (overflow) atomicOr(&ctr[CTR_ERR], ERR_G_CAP);
+}
+
 // ------------------------------------------------------------------ IB loop
 // One persistent kernel runs the whole correction loop of a step, one CTA
-// per SM, with a bounded grid barrier between the phases that need all
-// markers (Jacobi iterations).  Phases:
-//   gather  (rho, j^0) of every band node from the post-stream state;
-//   N iterations over the markers (16 lanes per marker, one per stencil
-//     node), each followed by a barrier;
-//   residual pass r^N, application of the summed correction to f on every
-//     band node, per-CTA partial sums of body force and torque; barrier;
-//   collide+stream of the band row segments (the rest of the lattice is
-//     handled concurrently by the band-free collide+stream launch), and the
-//     final force sums.
+// per SM, with a bounded grid barrier between phases that read other CTAs'
+// results.  With J*^0_l the interpolated momentum of the uncorrected state,
+// b_l = rho*_l U_l - J*^0_l and A^0 = 0, the Jacobi iteration of Eqs. 22-27
+// on the momentum is
+//     dj^n = b - G A^n,   A^{n+1} = A^n + dj^n,   r^n = max_l |dj^n_l| / rho*_l,
+// because spreading and interpolating are linear (node momentum
+// j^n(x) = j^0(x) + sum_m W_m(x) ds_m A^n_m).  The second moments do not feed
+// back, so their deviations are formed once every A^n is known:
+//     C_l = sum_n (rho*_l U U - Pi*^n_l),  sum_n Pi*^n_l =
+//           sum_x W_l(x) / rho(x) sum_n j^n(x) j^n(x).
+// Phases (| = grid barrier):
+//   gather rho, j^0 of every band node | interpolate rho*, J*^0 and do
+//   iteration 0 | iterations 1..N-1, each | residual r^N; per band node the
+//   spread D^N and sum_n j^n j^n | per marker C_l | apply the summed
+//   correction to f on every band node (Eq. 27 summed over n), FP64 partial
+//   force sums | collide+stream of the band row segments, force totals.
 template <int P>
 struct IbArgs {
   typedef typename Prec<P>::S S;
@@ -181,15 +235,16 @@ struct IbArgs {
   int* ctr;
   int bcap, M, N, nb, nseg_x;
   const int* bnode;
-  R* brho;
-  R* bJ;
+  R* bq;                      // [bcap][8]: rho, j0x, j0y, S2xx, S2xy, S2yy, dJx, dJy
   const int* bcnt;
   const Ent<R>* ent;
   const int* band_of;
   const R* W;
-  R* A0;
-  R* A1;
-  R* Cm;
+  const Ent<R>* G;
+  const int* gcnt;
+  R* mq;                      // [M][4]: rho*, b_x, b_y, pad
+  R* Ah;                      // [N+1][M][2] accumulated momentum deviations
+  R* Cm;                      // [M][3]
   const R* Ux;
   const R* Uy;
   R* resid;
@@ -220,7 +275,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* ctr) {
     } else {
       const long long t0 = clock64();
       while (*gen == g0) {
-        __nanosleep(64);
+        __nanosleep(32);
         if (clock64() - t0 > kBarrierCycles) { atomicOr(&ctr[CTR_ERR], ERR_BARRIER); break; }
       }
     }
@@ -230,16 +285,18 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* ctr) {
 }
 
 template <class R>
-__device__ __forceinline__ R block_max(R v) {
+__device__ __forceinline__ void block_max_to(R v, R* dst) {
   __shared__ R red[kIbThreads / 32];
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  R m = red[0];
-  for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
+  if (threadIdx.x == 0) {
+    R m = red[0];
+    for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
+    if (m > R(0) || m != m) AtomicBits<R>::max(dst, m);
+  }
   __syncthreads();
-  return m;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -254,82 +311,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// Current momentum of band node b: j^0 plus the spread of the accumulated
-// deviations of the markers covering it, in ascending marker order.
-template <class R>
-__device__ __forceinline__ void band_momentum(int b, const R* __restrict__ bJ, const int* __restrict__ bcnt,
-                                              const Ent<R>* __restrict__ ent, const R* __restrict__ Acc,
-                                              R& jx, R& jy) {
-  jx = bJ[2 * b];
-  jy = bJ[2 * b + 1];
-  const int n = bcnt[b];
-  const Ent<R>* e = ent + (long long)b * kBandCap;
+// dj = b_l - sum_m G_lm A_m for marker l (row in ascending m).
+template <class R, class Args>
+__device__ __forceinline__ void deviation(const Args& a, int l, const R* __restrict__ An, R& djx, R& djy) {
+  djx = a.mq[4 * l + 1];
+  djy = a.mq[4 * l + 2];
+  const int n = a.gcnt[l];
+  const Ent<R>* row = a.G + (long long)l * kGCap;
   for (int k = 0; k < n; ++k) {
-    const Ent<R> q = e[k];
-    jx += q.w * Acc[2 * q.m];
-    jy += q.w * Acc[2 * q.m + 1];
+    const Ent<R> q = row[k];
+    djx -= q.w * An[2 * q.m];
+    djy -= q.w * An[2 * q.m + 1];
   }
-}
-
-// One pass over all markers, two markers per warp: each lane forms its
-// stencil node's weighted rho, j, Pi = j j / rho; a 16-lane butterfly gives
-// (rho*, j*, Pi*) (Eq. 22b with Eq. 28 in moment form); lane 0 of the marker
-// forms the residual |j*/rho* - U| and, when updating, the deviation
-// (dj, dPi) added to A (Jacobi: read Ain, write Aout) and C.  Returns the
-// largest residual seen by this thread.
-template <class R>
-__device__ R marker_pass_impl(const int M, const int* __restrict__ band_of, const R* __restrict__ W,
-                              const R* __restrict__ brho, const R* __restrict__ bJ,
-                              const int* __restrict__ bcnt, const Ent<R>* __restrict__ ent,
-                              const R* __restrict__ Ain, R* __restrict__ Aout, R* __restrict__ Cm,
-                              const R* __restrict__ Ux, const R* __restrict__ Uy, bool first, bool update) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarp = (gridDim.x * blockDim.x) >> 5;
-  R rmax = R(0);
-  for (int base = 2 * warp; base < M; base += 2 * nwarp) {
-    const int l = base + (lane >> 4);
-    const bool valid = l < M;
-    const int t = l * kStencil + (lane & 15);
-    const int b = valid ? band_of[t] : -1;
-    R w = R(0), rho = R(1), jx = R(0), jy = R(0);
-    if (b >= 0) {
-      w = W[t];
-      rho = brho[b];
-      if (first) { jx = bJ[2 * b]; jy = bJ[2 * b + 1]; }
-      else band_momentum<R>(b, bJ, bcnt, ent, Ain, jx, jy);
-    }
-    const R inv = R(1) / rho;
-    R v0 = w * rho, v1 = w * jx, v2 = w * jy;
-    R v3 = w * (jx * jx * inv), v4 = w * (jx * jy * inv), v5 = w * (jy * jy * inv);
-#pragma unroll
-    for (int off = kStencil / 2; off >= 1; off >>= 1) {
-      v0 += __shfl_xor_sync(0xffffffffu, v0, off);
-      v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-      v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-      v3 += __shfl_xor_sync(0xffffffffu, v3, off);
-      v4 += __shfl_xor_sync(0xffffffffu, v4, off);
-      v5 += __shfl_xor_sync(0xffffffffu, v5, off);
-    }
-    if (valid && (lane & 15) == 0) {
-      const R ux = Ux[l], uy = Uy[l];
-      const R rs = v0;
-      const R ex = v1 / rs - ux, ey = v2 / rs - uy;
-      rmax = nanmax(rmax, (R)sqrt(ex * ex + ey * ey));
-      if (update) {
-        const R djx = rs * ux - v1, djy = rs * uy - v2;
-        const R dpxx = rs * ux * ux - v3, dpxy = rs * ux * uy - v4, dpyy = rs * uy * uy - v5;
-        if (first) {
-          Aout[2 * l] = djx; Aout[2 * l + 1] = djy;
-          Cm[3 * l] = dpxx; Cm[3 * l + 1] = dpxy; Cm[3 * l + 2] = dpyy;
-        } else {
-          Aout[2 * l] = Ain[2 * l] + djx; Aout[2 * l + 1] = Ain[2 * l + 1] + djy;
-          Cm[3 * l] += dpxx; Cm[3 * l + 1] += dpxy; Cm[3 * l + 2] += dpyy;
-        }
-      }
-    }
-  }
-  return rmax;
 }
 
 template <int P, int PAR, bool MACRO>
@@ -338,9 +331,10 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const int nband = min(a.ctr[CTR_NBAND], a.bcap);
+  const int M = a.M, N = a.N;
   long long where;
 
-  // gather (rho, j^0) at every band node
+  // gather rho and j^0 at every band node
   for (int b = tid; b < nband; b += nth) {
     const int n = a.bnode[b];
     const int x = n % a.g.nx, y = n / a.g.nx;
@@ -348,45 +342,136 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) p[i] = post_stream<P>(a.g, a.c, a.A, PAR, x, y, i, where);
     moments9<R>(p, rho, jx, jy);
-    a.brho[b] = rho;
-    a.bJ[2 * b] = jx;
-    a.bJ[2 * b + 1] = jy;
+    a.bq[8 * b] = rho;
+    a.bq[8 * b + 1] = jx;
+    a.bq[8 * b + 2] = jy;
   }
   grid_barrier(a.bar, a.ctr);
 
-  // correction iterations (Eqs. 22-27), Jacobi over markers
-  R* acc[2] = {a.A0, a.A1};
-  for (int n = 0; n < a.N; ++n) {
-    const R r = marker_pass_impl<R>(a.M, a.band_of, a.W, a.brho, a.bJ, a.bcnt, a.ent, acc[n & 1],
-                                    acc[(n + 1) & 1], a.Cm, a.Ux, a.Uy, n == 0, true);
-    const R m = block_max<R>(r);
-    if (threadIdx.x == 0 && (m > R(0) || m != m)) AtomicBits<R>::max(a.resid + n, m);
+  // interpolate rho*, J*^0 (Eq. 22b with Eq. 28 in moment form), b_l, and
+  // iteration 0 (A^0 = 0, so dj^0 = b)
+  {
+    R rmax = R(0);
+    for (int l = tid; l < M; l += nth) {
+      R rs = R(0), jx = R(0), jy = R(0);
+#pragma unroll 4
+      for (int s = 0; s < kStencil; ++s) {
+        const int b = a.band_of[l * kStencil + s];
+        if (b < 0) continue;
+        const R w = a.W[l * kStencil + s];
+        rs += w * a.bq[8 * b];
+        jx += w * a.bq[8 * b + 1];
+        jy += w * a.bq[8 * b + 2];
+      }
+      const R bx = rs * a.Ux[l] - jx, by = rs * a.Uy[l] - jy;
+      a.mq[4 * l] = rs;
+      a.mq[4 * l + 1] = bx;
+      a.mq[4 * l + 2] = by;
+      a.Ah[2 * l] = R(0);
+      a.Ah[2 * l + 1] = R(0);
+      if (N > 0) {
+        a.Ah[2 * M + 2 * l] = bx;
+        a.Ah[2 * M + 2 * l + 1] = by;
+      }
+      rmax = nanmax(rmax, (R)(sqrt(bx * bx + by * by) / rs));
+    }
+    block_max_to<R>(rmax, a.resid);
+  }
+  grid_barrier(a.bar, a.ctr);
+
+  // iterations 1..N-1 (Jacobi: read A^n, write A^{n+1})
+  for (int n = 1; n < N; ++n) {
+    const R* An = a.Ah + (long long)n * 2 * M;
+    R* An1 = a.Ah + (long long)(n + 1) * 2 * M;
+    R rmax = R(0);
+    for (int l = tid; l < M; l += nth) {
+      R djx, djy;
+      deviation<R>(a, l, An, djx, djy);
+      An1[2 * l] = An[2 * l] + djx;
+      An1[2 * l + 1] = An[2 * l + 1] + djy;
+      rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
+    }
+    block_max_to<R>(rmax, a.resid + n);
     grid_barrier(a.bar, a.ctr);
   }
-  const R* afin = acc[a.N & 1];
 
-  // final residual r^N (no correction)
+  // final residual r^N, and per band node the final spread D^N and
+  // sum_n j^n j^n over the iterations
   {
-    const R r = marker_pass_impl<R>(a.M, a.band_of, a.W, a.brho, a.bJ, a.bcnt, a.ent, afin, nullptr,
-                                    nullptr, a.Ux, a.Uy, a.N == 0, false);
-    const R m = block_max<R>(r);
-    if (threadIdx.x == 0 && (m > R(0) || m != m)) AtomicBits<R>::max(a.resid + a.N, m);
+    const R* AN = a.Ah + (long long)N * 2 * M;
+    R rmax = R(0);
+    for (int l = tid; l < M; l += nth) {
+      R djx, djy;
+      deviation<R>(a, l, AN, djx, djy);
+      rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
+    }
+    block_max_to<R>(rmax, a.resid + N);
   }
+  if (N > 0) {
+    for (int b = tid; b < nband; b += nth) {
+      const R j0x = a.bq[8 * b + 1], j0y = a.bq[8 * b + 2];
+      const int cnt = a.bcnt[b];
+      const Ent<R>* e = a.ent + (long long)b * kBandCap;
+      R sxx = R(0), sxy = R(0), syy = R(0), dx = R(0), dy = R(0);
+      for (int n = 0; n <= N; ++n) {
+        const R* An = a.Ah + (long long)n * 2 * M;
+        R px = R(0), py = R(0);
+        for (int k = 0; k < cnt; ++k) {
+          const Ent<R> q = e[k];
+          px += q.w * An[2 * q.m];
+          py += q.w * An[2 * q.m + 1];
+        }
+        if (n < N) {
+          const R jx = j0x + px, jy = j0y + py;
+          sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
+        } else {
+          dx = px; dy = py;
+        }
+      }
+      a.bq[8 * b + 3] = sxx;
+      a.bq[8 * b + 4] = sxy;
+      a.bq[8 * b + 5] = syy;
+      a.bq[8 * b + 6] = dx;
+      a.bq[8 * b + 7] = dy;
+    }
+  }
+  grid_barrier(a.bar, a.ctr);
+
+  // second-moment deviations summed over the iterations
+  if (N > 0) {
+    for (int l = tid; l < M; l += nth) {
+      R pxx = R(0), pxy = R(0), pyy = R(0);
+#pragma unroll 4
+      for (int s = 0; s < kStencil; ++s) {
+        const int b = a.band_of[l * kStencil + s];
+        if (b < 0) continue;
+        const R w = a.W[l * kStencil + s] / a.bq[8 * b];
+        pxx += w * a.bq[8 * b + 3];
+        pxy += w * a.bq[8 * b + 4];
+        pyy += w * a.bq[8 * b + 5];
+      }
+      const R rs = a.mq[4 * l], ux = a.Ux[l], uy = a.Uy[l];
+      a.Cm[3 * l] = R(N) * rs * ux * ux - pxx;
+      a.Cm[3 * l + 1] = R(N) * rs * ux * uy - pxy;
+      a.Cm[3 * l + 2] = R(N) * rs * uy * uy - pyy;
+    }
+  }
+  grid_barrier(a.bar, a.ctr);
 
   // Eq. 27 summed over the iterations: f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi]
-  if (a.N > 0) {
+  const R* AN = a.Ah + (long long)N * 2 * M;
+  if (N > 0) {
     for (int b = tid; b < nband; b += nth) {
-      R jx = R(0), jy = R(0), pxx = R(0), pxy = R(0), pyy = R(0);
+      R pxx = R(0), pxy = R(0), pyy = R(0);
       const int cnt = a.bcnt[b];
       const Ent<R>* e = a.ent + (long long)b * kBandCap;
       for (int k = 0; k < cnt; ++k) {
         const Ent<R> q = e[k];
-        jx += q.w * afin[2 * q.m];
-        jy += q.w * afin[2 * q.m + 1];
         pxx += q.w * a.Cm[3 * q.m];
         pxy += q.w * a.Cm[3 * q.m + 1];
         pyy += q.w * a.Cm[3 * q.m + 2];
       }
+      const R jx = a.bq[8 * b + 6], jy = a.bq[8 * b + 7];
       const int n = a.bnode[b];
       const int x = n % a.g.nx, y = n / a.g.nx;
 #pragma unroll
@@ -401,10 +486,10 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
   }
 
   // Eq. 29: per-CTA partial force and torque of each body over a fixed
-  // chunk of markers, F_l = -ds_l A_l, T_l = (X_l - x_c) x F_l (FP64).
+  // chunk of markers, F_l = -ds_l A^N_l, T_l = (X_l - x_c) x F_l (FP64).
   __shared__ double sh[kIbThreads];
-  const int chunk = (a.M + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * chunk, hi = min(a.M, lo + chunk);
+  const int chunk = (M + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(M, lo + chunk);
   if (a.nb > 0 && lo < hi) {
     const int b0 = a.mbody[lo], b1 = a.mbody[hi - 1];
     for (int bd = b0; bd <= b1; ++bd) {
@@ -412,7 +497,7 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       const int l0 = max(lo, B.m0), l1 = min(hi, B.m1);
       double fx = 0.0, fy = 0.0, tq = 0.0;
       for (int l = l0 + (int)threadIdx.x; l < l1; l += blockDim.x) {
-        const double Fx = -a.ds[l] * (double)afin[2 * l], Fy = -a.ds[l] * (double)afin[2 * l + 1];
+        const double Fx = -a.ds[l] * (double)AN[2 * l], Fy = -a.ds[l] * (double)AN[2 * l + 1];
         fx += Fx;
         fy += Fy;
         tq += (a.X[l] - B.xc[0]) * Fy - (a.Y[l] - B.xc[1]) * Fx;
@@ -556,6 +641,8 @@ static void band_build_t(const Ctx& h, cudaStream_t s) {
   k_band_sort<R><<<blocks_for(h.bcap, 128), 128, 0, s>>>(h.dctr, h.dbcnt, (Ent<R>*)h.dent, h.bcap);
   k_band_segments<<<blocks_for(h.bcap, 256), 256, 0, s>>>(h.geom, h.dbnode, h.dsegflag, h.dseglist, h.dctr,
                                                           h.nseg_x, h.bcap, h.segcap);
+  k_build_g<R><<<blocks_for(h.nm, 64), 64, 0, s>>>(h.nm, h.dband_of, (const R*)h.dW, h.dbcnt,
+                                                    (const Ent<R>*)h.dent, (Ent<R>*)h.dG, h.dgcnt, h.dctr);
 }
 
 void launch_band_build(const Ctx& h, cudaStream_t s) {
@@ -580,14 +667,15 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   a.nb = h.nb;
   a.nseg_x = h.nseg_x;
   a.bnode = h.dbnode;
-  a.brho = (R*)h.dbrho;
-  a.bJ = (R*)h.dbJ0;
+  a.bq = (R*)h.dbq;
   a.bcnt = h.dbcnt;
   a.ent = (const Ent<R>*)h.dent;
   a.band_of = h.dband_of;
   a.W = (const R*)h.dW;
-  a.A0 = (R*)h.dA0;
-  a.A1 = (R*)h.dA1;
+  a.G = (const Ent<R>*)h.dG;
+  a.gcnt = h.dgcnt;
+  a.mq = (R*)h.dmq;
+  a.Ah = (R*)h.dAh;
   a.Cm = (R*)h.dCm;
   a.Ux = (const R*)h.dUx;
   a.Uy = (const R*)h.dUy;

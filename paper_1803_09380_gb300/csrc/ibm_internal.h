@@ -22,7 +22,7 @@ struct BodyDev {
   double F_ib[2], T_ib;     // Eq. 29 sums of the last step (no internal-mass terms)
 };
 
-enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4, ERR_BARRIER = 8 };
+enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4, ERR_BARRIER = 8, ERR_G_CAP = 16 };
 
 // One entry of a band node's list of covering markers: marker id and its
 // spreading weight W_l(x) ds_l.
@@ -33,6 +33,7 @@ struct Ent {
 };
 
 constexpr int kIbThreads = 256;                  // threads per correction-loop CTA
+constexpr int kGCap = 64;                        // coupled markers per marker (G row)
 constexpr long long kBarrierCycles = 4000000000LL; // ~2 s at 2 GHz: grid-barrier wait limit
 
 // Device counters: band nodes, band row segments, error bits.
@@ -89,9 +90,12 @@ struct Ctx {
   int* dbnode = nullptr;                     // [bcap] node of band entry
   int* dbcnt = nullptr;                      // [bcap] covering markers
   void* dent = nullptr;                      // [bcap * kBandCap] Ent<R>, ascending marker id
-  void *dbrho = nullptr, *dbJ0 = nullptr;    // [bcap], [2 bcap] (R)
-  void *dA0 = nullptr, *dA1 = nullptr;       // [2 nm] accumulated momentum deviation (R)
-  void* dCm = nullptr;                       // [3 nm] accumulated second-moment deviation (R)
+  void* dbq = nullptr;                       // [bcap][8] band-node quantities (R)
+  void* dmq = nullptr;                       // [nm][4] rho*, b (R)
+  void* dAh = nullptr;                       // [n_corr+1][nm][2] momentum deviations A^n (R)
+  void* dCm = nullptr;                       // [nm][3] summed second-moment deviation (R)
+  void* dG = nullptr;                        // [nm][kGCap] Ent<R> marker coupling rows
+  int* dgcnt = nullptr;                      // [nm]
   void* dresid = nullptr;                    // [n_corr + 1] (R)
   int* dctr = nullptr;                       // CTR_* counters
   int nseg_x = 0;                            // 32-node segments per row
