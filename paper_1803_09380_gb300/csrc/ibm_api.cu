@@ -357,7 +357,7 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
     c.macro = dev_alloc(c, c.r_bytes * 3 * (size_t)d.nx * d.ny);
     c.dnode2band = (int*)dev_alloc(c, sizeof(int) * (size_t)d.nx * d.ny);
     c.dctr = (int*)dev_alloc(c, CTR_COUNT * sizeof(int));
-    c.dbar = (unsigned*)dev_alloc(c, 2 * sizeof(unsigned));
+    c.dbar = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long));
     c.dsegflag = (int*)dev_alloc(c, sizeof(int) * (size_t)c.nseg_x * d.ny);
     c.dresid = dev_alloc(c, c.r_bytes * (d.n_corr + 1));
     if (!c.f || !c.macro || !c.dnode2band || !c.dctr || !c.dresid || !c.dsegflag || !c.dbar) {
@@ -368,7 +368,7 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
     if (cudaMemsetAsync(c.f, 0, c.s_bytes * 9 * (size_t)c.geom.plane, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)d.nx * d.ny, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dctr, 0, CTR_COUNT * sizeof(int), c.stream) != cudaSuccess ||
-        cudaMemsetAsync(c.dbar, 0, 2 * sizeof(unsigned), c.stream) != cudaSuccess ||
+        cudaMemsetAsync(c.dbar, 0, sizeof(unsigned long long), c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dsegflag, 0, sizeof(int) * (size_t)c.nseg_x * d.ny, c.stream) != cudaSuccess ||
         cudaMemsetAsync(c.dresid, 0, c.r_bytes * (d.n_corr + 1), c.stream) != cudaSuccess) {
       c.err = std::string("device memset failed: ") + cudaGetErrorString(cudaGetLastError());

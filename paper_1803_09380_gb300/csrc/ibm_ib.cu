@@ -255,29 +255,25 @@ struct IbArgs {
   const double* Y;
   const double* ds;
   double* fpart;              // [gridDim][nb][3]
-  unsigned* bar;              // [0] arrivals, [1] generation
+  unsigned long long* bar;    // grid-barrier arrivals (monotonic)
 };
 
-// Grid barrier for a launch whose CTAs are all resident (one per SM).  The
-// wait is bounded: after kBarrierCycles the CTA records ERR_BARRIER and goes
-// on, so a broken launch ends with an error status instead of hanging.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, int* ctr) {
+// Grid barrier for a launch whose CTAs are all resident (one per SM).  A
+// 64-bit arrival counter only grows: the k-th barrier of all launches is
+// complete when it reaches k * gridDim.x.  The wait is bounded: after
+// kBarrierCycles the CTA records ERR_BARRIER and goes on, so a broken launch
+// ends with an error status instead of hanging.
+__device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
     __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g0) {
-        __nanosleep(32);
-        if (clock64() - t0 > kBarrierCycles) { atomicOr(&ctr[CTR_ERR], ERR_BARRIER); break; }
-      }
+    const unsigned long long g = gridDim.x;
+    const unsigned long long t = atomicAdd(bar, 1ull) + 1ull;
+    const unsigned long long target = ((t + g - 1) / g) * g;
+    volatile unsigned long long* v = bar;
+    const long long t0 = clock64();
+    while (*v < target) {
+      if (clock64() - t0 > kBarrierCycles) { atomicOr(&ctr[CTR_ERR], ERR_BARRIER); break; }
     }
     __threadfence();
   }
@@ -311,18 +307,43 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+template <class R> struct Vec2;
+template <> struct Vec2<float> { typedef float2 T; };
+template <> struct Vec2<double> { typedef double2 T; };
+
+// sum over a sparse list (marker, weight) of weight * A[marker] (two
+// components), in list order; entries are gathered eight at a time so their
+// loads, and then the eight A loads, are in flight together.
+template <class R>
+__device__ __forceinline__ void sparse_dot(const Ent<R>* __restrict__ e, int n, const R* __restrict__ A,
+                                           int pad_m, R& sx, R& sy) {
+  typedef typename Vec2<R>::T V;
+  const V* Av = reinterpret_cast<const V*>(A);
+  for (int k0 = 0; k0 < n; k0 += 8) {
+    Ent<R> q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (k0 + j < n) q[j] = e[k0 + j];
+      else { q[j].m = pad_m; q[j].w = R(0); }
+    }
+    V v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = Av[q[j].m];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      sx += q[j].w * v[j].x;
+      sy += q[j].w * v[j].y;
+    }
+  }
+}
+
 // dj = b_l - sum_m G_lm A_m for marker l (row in ascending m).
 template <class R, class Args>
 __device__ __forceinline__ void deviation(const Args& a, int l, const R* __restrict__ An, R& djx, R& djy) {
-  djx = a.mq[4 * l + 1];
-  djy = a.mq[4 * l + 2];
-  const int n = a.gcnt[l];
-  const Ent<R>* row = a.G + (long long)l * kGCap;
-  for (int k = 0; k < n; ++k) {
-    const Ent<R> q = row[k];
-    djx -= q.w * An[2 * q.m];
-    djy -= q.w * An[2 * q.m + 1];
-  }
+  R sx = R(0), sy = R(0);
+  sparse_dot<R>(a.G + (long long)l * kGCap, a.gcnt[l], An, l, sx, sy);
+  djx = a.mq[4 * l + 1] - sx;
+  djy = a.mq[4 * l + 2] - sy;
 }
 
 template <int P, int PAR, bool MACRO>
@@ -354,14 +375,19 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
     R rmax = R(0);
     for (int l = tid; l < M; l += nth) {
       R rs = R(0), jx = R(0), jy = R(0);
-#pragma unroll 4
+      int bb[kStencil];
+      R ww[kStencil];
+#pragma unroll
       for (int s = 0; s < kStencil; ++s) {
         const int b = a.band_of[l * kStencil + s];
-        if (b < 0) continue;
-        const R w = a.W[l * kStencil + s];
-        rs += w * a.bq[8 * b];
-        jx += w * a.bq[8 * b + 1];
-        jy += w * a.bq[8 * b + 2];
+        bb[s] = b < 0 ? 0 : b;
+        ww[s] = b < 0 ? R(0) : a.W[l * kStencil + s];
+      }
+#pragma unroll
+      for (int s = 0; s < kStencil; ++s) {
+        rs += ww[s] * a.bq[8 * bb[s]];
+        jx += ww[s] * a.bq[8 * bb[s] + 1];
+        jy += ww[s] * a.bq[8 * bb[s] + 2];
       }
       const R bx = rs * a.Ux[l] - jx, by = rs * a.Uy[l] - jy;
       a.mq[4 * l] = rs;
@@ -413,21 +439,14 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       const int cnt = a.bcnt[b];
       const Ent<R>* e = a.ent + (long long)b * kBandCap;
       R sxx = R(0), sxy = R(0), syy = R(0), dx = R(0), dy = R(0);
-      for (int n = 0; n <= N; ++n) {
-        const R* An = a.Ah + (long long)n * 2 * M;
+#pragma unroll 2
+      for (int n = 0; n < N; ++n) {
         R px = R(0), py = R(0);
-        for (int k = 0; k < cnt; ++k) {
-          const Ent<R> q = e[k];
-          px += q.w * An[2 * q.m];
-          py += q.w * An[2 * q.m + 1];
-        }
-        if (n < N) {
-          const R jx = j0x + px, jy = j0y + py;
-          sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
-        } else {
-          dx = px; dy = py;
-        }
+        sparse_dot<R>(e, cnt, a.Ah + (long long)n * 2 * M, 0, px, py);
+        const R jx = j0x + px, jy = j0y + py;
+        sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
       }
+      sparse_dot<R>(e, cnt, a.Ah + (long long)N * 2 * M, 0, dx, dy);
       a.bq[8 * b + 3] = sxx;
       a.bq[8 * b + 4] = sxy;
       a.bq[8 * b + 5] = syy;
@@ -441,14 +460,20 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
   if (N > 0) {
     for (int l = tid; l < M; l += nth) {
       R pxx = R(0), pxy = R(0), pyy = R(0);
-#pragma unroll 4
+      int bb[kStencil];
+      R ww[kStencil];
+#pragma unroll
       for (int s = 0; s < kStencil; ++s) {
         const int b = a.band_of[l * kStencil + s];
-        if (b < 0) continue;
-        const R w = a.W[l * kStencil + s] / a.bq[8 * b];
-        pxx += w * a.bq[8 * b + 3];
-        pxy += w * a.bq[8 * b + 4];
-        pyy += w * a.bq[8 * b + 5];
+        bb[s] = b < 0 ? 0 : b;
+        ww[s] = b < 0 ? R(0) : a.W[l * kStencil + s];
+      }
+#pragma unroll
+      for (int s = 0; s < kStencil; ++s) {
+        const R w = ww[s] / a.bq[8 * bb[s]];
+        pxx += w * a.bq[8 * bb[s] + 3];
+        pxy += w * a.bq[8 * bb[s] + 4];
+        pyy += w * a.bq[8 * bb[s] + 5];
       }
       const R rs = a.mq[4 * l], ux = a.Ux[l], uy = a.Uy[l];
       a.Cm[3 * l] = R(N) * rs * ux * ux - pxx;
@@ -465,11 +490,26 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       R pxx = R(0), pxy = R(0), pyy = R(0);
       const int cnt = a.bcnt[b];
       const Ent<R>* e = a.ent + (long long)b * kBandCap;
-      for (int k = 0; k < cnt; ++k) {
-        const Ent<R> q = e[k];
-        pxx += q.w * a.Cm[3 * q.m];
-        pxy += q.w * a.Cm[3 * q.m + 1];
-        pyy += q.w * a.Cm[3 * q.m + 2];
+      for (int k0 = 0; k0 < cnt; k0 += 8) {
+        Ent<R> q[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (k0 + j < cnt) q[j] = e[k0 + j];
+          else { q[j].m = 0; q[j].w = R(0); }
+        }
+        R c0[8], c1[8], c2[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          c0[j] = a.Cm[3 * q[j].m];
+          c1[j] = a.Cm[3 * q[j].m + 1];
+          c2[j] = a.Cm[3 * q[j].m + 2];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          pxx += q[j].w * c0[j];
+          pxy += q[j].w * c1[j];
+          pyy += q[j].w * c2[j];
+        }
       }
       const R jx = a.bq[8 * b + 6], jy = a.bq[8 * b + 7];
       const int n = a.bnode[b];

@@ -27,7 +27,7 @@ enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4, ERR_BARRIER = 8, ERR
 // One entry of a band node's list of covering markers: marker id and its
 // spreading weight W_l(x) ds_l.
 template <class R>
-struct Ent {
+struct alignas(2 * sizeof(R) > 8 ? 16 : 8) Ent {
   int m;
   R w;
 };
@@ -104,7 +104,7 @@ struct Ctx {
   int* dseglist = nullptr;                   // [segcap] band segments
   BodyDev* dbodies = nullptr;
   double* dfpart = nullptr;                  // [ib_grid][nb][3] force partial sums
-  unsigned* dbar = nullptr;                  // grid barrier state of the correction kernel
+  unsigned long long* dbar = nullptr;        // grid-barrier arrivals of the correction kernel
   int ib_grid = 0;                           // CTAs of the correction kernel (one per SM)
   bool band_valid = false;
 
