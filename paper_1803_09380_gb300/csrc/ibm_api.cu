@@ -219,6 +219,10 @@ ibm_status upload_markers(Ctx* h) {
                             cudaMemcpyHostToDevice, c.stream));
   IBM_CK(h, cudaMemsetAsync(c.dAh, 0, R * 2 * (size_t)M * (c.desc.n_corr + 1), c.stream));
   IBM_CK(h, cudaMemsetAsync(c.dCm, 0, R * 3 * (size_t)M, c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dG, 0, (R == 8 ? sizeof(Ent<double>) : sizeof(Ent<float>)) * (size_t)M * kGCap,
+                            c.stream));
+  IBM_CK(h, cudaMemsetAsync(c.dent, 0, (R == 8 ? sizeof(Ent<double>) : sizeof(Ent<float>)) *
+                                           (size_t)c.bcap * kBandCap, c.stream));
   IBM_CK(h, cudaMemsetAsync(c.dbcnt, 0, sizeof(int) * c.bcap, c.stream));
   IBM_CK(h, cudaStreamSynchronize(c.stream));   // host vectors are temporaries
   c.band_valid = false;

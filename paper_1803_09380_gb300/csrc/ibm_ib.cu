@@ -337,11 +337,37 @@ __device__ __forceinline__ void sparse_dot(const Ent<R>* __restrict__ e, int n, 
   }
 }
 
+// Same sum for a stored row of at least 8 slots whose length is read from
+// cntp: the first eight entries are loaded together with the length, so the
+// common short row costs two dependent memory trips.
+template <class R>
+__device__ __forceinline__ void row_dot(const Ent<R>* __restrict__ e, const int* __restrict__ cntp,
+                                        const R* __restrict__ A, int pad_m, R& sx, R& sy) {
+  typedef typename Vec2<R>::T V;
+  const V* Av = reinterpret_cast<const V*>(A);
+  Ent<R> q[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) q[j] = e[j];
+  const int n = *cntp;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (j >= n) { q[j].m = pad_m; q[j].w = R(0); }
+  V v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = Av[q[j].m];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    sx += q[j].w * v[j].x;
+    sy += q[j].w * v[j].y;
+  }
+  if (n > 8) sparse_dot<R>(e + 8, n - 8, A, pad_m, sx, sy);
+}
+
 // dj = b_l - sum_m G_lm A_m for marker l (row in ascending m).
 template <class R, class Args>
 __device__ __forceinline__ void deviation(const Args& a, int l, const R* __restrict__ An, R& djx, R& djy) {
   R sx = R(0), sy = R(0);
-  sparse_dot<R>(a.G + (long long)l * kGCap, a.gcnt[l], An, l, sx, sy);
+  row_dot<R>(a.G + (long long)l * kGCap, a.gcnt + l, An, l, sx, sy);
   djx = a.mq[4 * l + 1] - sx;
   djy = a.mq[4 * l + 2] - sy;
 }
@@ -434,19 +460,38 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
     block_max_to<R>(rmax, a.resid + N);
   }
   if (N > 0) {
+    typedef typename Vec2<R>::T V;
     for (int b = tid; b < nband; b += nth) {
       const R j0x = a.bq[8 * b + 1], j0y = a.bq[8 * b + 2];
-      const int cnt = a.bcnt[b];
       const Ent<R>* e = a.ent + (long long)b * kBandCap;
+      Ent<R> q[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) q[j] = e[j];
+      const int cnt = a.bcnt[b];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j >= cnt) { q[j].m = 0; q[j].w = R(0); }
       R sxx = R(0), sxy = R(0), syy = R(0), dx = R(0), dy = R(0);
-#pragma unroll 2
-      for (int n = 0; n < N; ++n) {
+#pragma unroll 4
+      for (int n = 0; n <= N; ++n) {
+        const V* Av = reinterpret_cast<const V*>(a.Ah + (long long)n * 2 * M);
+        V v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = Av[q[j].m];
         R px = R(0), py = R(0);
-        sparse_dot<R>(e, cnt, a.Ah + (long long)n * 2 * M, 0, px, py);
-        const R jx = j0x + px, jy = j0y + py;
-        sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          px += q[j].w * v[j].x;
+          py += q[j].w * v[j].y;
+        }
+        if (cnt > 8) sparse_dot<R>(e + 8, cnt - 8, a.Ah + (long long)n * 2 * M, 0, px, py);
+        if (n < N) {
+          const R jx = j0x + px, jy = j0y + py;
+          sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
+        } else {
+          dx = px; dy = py;
+        }
       }
-      sparse_dot<R>(e, cnt, a.Ah + (long long)N * 2 * M, 0, dx, dy);
       a.bq[8 * b + 3] = sxx;
       a.bq[8 * b + 4] = sxy;
       a.bq[8 * b + 5] = syy;
@@ -566,14 +611,18 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
     }
   }
 
-  // body totals in fixed order over the CTA chunks
-  if (blockIdx.x == 0) {
-    for (int bd = threadIdx.x; bd < a.nb; bd += blockDim.x) {
-      BodyDev& B = a.bodies[bd];
-      const int k0 = B.m0 / chunk, k1 = (B.m1 - 1) / chunk;
-      double f[3] = {0.0, 0.0, 0.0};
-      for (int k = k0; k <= k1; ++k)
-        for (int q = 0; q < 3; ++q) f[q] += a.fpart[((long long)k * a.nb + bd) * 3 + q];
+  // body totals: one body per CTA, fixed-shape reduction over the chunks
+  for (int bd = blockIdx.x; bd < a.nb; bd += gridDim.x) {
+    BodyDev& B = a.bodies[bd];
+    const int k0 = B.m0 / chunk, k1 = (B.m1 - 1) / chunk;
+    double f[3];
+    for (int q = 0; q < 3; ++q) {
+      double v = 0.0;
+      for (int k = k0 + (int)threadIdx.x; k <= k1; k += blockDim.x)
+        v += a.fpart[((long long)k * a.nb + bd) * 3 + q];
+      f[q] = block_sum(v, sh);
+    }
+    if (threadIdx.x == 0) {
       B.F_ib[0] = f[0];
       B.F_ib[1] = f[1];
       B.T_ib = f[2];

@@ -119,4 +119,170 @@ __device__ __forceinline__ void odd_node(const Geom& g, const StepConsts<typenam
   }
 }
 
+// ------------------------------------------------------------------ vectors
+// VEC consecutive nodes per thread, moved as one 16-byte access per slot.
+template <int P>
+struct VecTraits {
+  typedef typename Prec<P>::S S;
+  static constexpr int VEC = 16 / (int)sizeof(S);
+};
+
+template <class S, int VEC>
+struct alignas(16) SVec {
+  S v[VEC];
+};
+
+template <class S, int VEC>
+__device__ __forceinline__ SVec<S, VEC> vload(const S* p) {
+  SVec<S, VEC> r;
+  *reinterpret_cast<uint4*>(&r) = *reinterpret_cast<const uint4*>(p);
+  return r;
+}
+template <class S, int VEC>
+__device__ __forceinline__ void vstore(S* p, const SVec<S, VEC>& r) {
+  *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(&r);
+}
+
+template <class S>
+__device__ __forceinline__ S shfl_up1(S v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <class S>
+__device__ __forceinline__ S shfl_down1(S v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// Collide VEC nodes whose pre-collision populations are p[i][k]
+// (arithmetic type), in place, writing macros if asked.
+template <int P, bool MACRO, int VEC>
+__device__ __forceinline__ void collide_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                            typename Prec<P>::R (&p)[9][VEC],
+                                            typename Prec<P>::R* __restrict__ mac, int x0, int y) {
+  typedef typename Prec<P>::R R;
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) {
+    R q[9], qs[9], rho, jx, jy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) q[i] = p[i][k];
+    if (x0 + k == 0 && g.bc[0] == BC_INLET) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) qs[i] = c.feq_in[i];
+      rho = c.rho0; jx = c.rho0 * c.inlet_u[0]; jy = c.rho0 * c.inlet_u[1];
+    } else {
+      bgk<R>(q, qs, rho, jx, jy, c.omega);
+    }
+    if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x0 + k, rho, jx, jy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) p[i][k] = qs[i];
+  }
+}
+
+// Even step for the VEC nodes x0.. of row y (all inside the lattice):
+// aligned vector loads of A[i], vector stores to A[opp(i)].
+template <int P, bool MACRO>
+__device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                         typename Prec<P>::S* __restrict__ A,
+                                         typename Prec<P>::R* __restrict__ mac, int x0, int y) {
+  typedef typename Prec<P>::S S;
+  typedef typename Prec<P>::R R;
+  constexpr int VEC = VecTraits<P>::VEC;
+  const long long base = (long long)y * g.nxp + x0;
+  R p[9][VEC];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const SVec<S, VEC> v = vload<S, VEC>(A + i * g.plane + base);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) p[i][k] = Prec<P>::ld(v.v[k], i);
+  }
+  collide_vec<P, MACRO, VEC>(g, c, p, mac, x0, y);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    SVec<S, VEC> v;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v.v[k] = Prec<P>::st(p[i][k], opp(i));
+    vstore<S, VEC>(A + opp(i) * g.plane + base, v);
+  }
+}
+
+// Odd step for one warp span of 32 * VEC consecutive nodes of row y that
+// holds no boundary node (every lane active; periodic wrap only across the
+// row ends).  Each lane owns nodes x0 .. x0+VEC-1.  Loads and stores are
+// aligned 16-byte vectors; the one-element shift of the directions with an
+// x component is done with warp shuffles.  Elements that cross to the
+// neighbouring span are read or written with scalar accesses by the thread
+// whose node owns the slot (lane 0 and lane 31), so spans never write each
+// other's slots.
+template <int P, bool MACRO>
+__device__ __forceinline__ void odd_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                        typename Prec<P>::S* __restrict__ A,
+                                        typename Prec<P>::R* __restrict__ mac, int x0, int y, int lane) {
+  typedef typename Prec<P>::S S;
+  typedef typename Prec<P>::R R;
+  constexpr int VEC = VecTraits<P>::VEC;
+  const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;              // left of the lane's nodes
+  const int xr = x0 + VEC == g.nx ? 0 : x0 + VEC;           // right of the lane's nodes
+  const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+  R p[9][VEC];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int sy = cy(i) > 0 ? ym : (cy(i) < 0 ? yp : y);
+    const int sl = opp(i);
+    const S* row = A + sl * g.plane + (long long)sy * g.nxp;
+    const SVec<S, VEC> v = vload<S, VEC>(row + x0);
+    if (cx(i) == 0) {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) p[i][k] = Prec<P>::ld(v.v[k], sl);
+    } else if (cx(i) > 0) {                                  // f_i(x) sits at x - 1
+      S left = shfl_up1<S>(v.v[VEC - 1]);
+      if (lane == 0) left = row[xl];
+      p[i][0] = Prec<P>::ld(left, sl);
+#pragma unroll
+      for (int k = 1; k < VEC; ++k) p[i][k] = Prec<P>::ld(v.v[k - 1], sl);
+    } else {                                                 // f_i(x) sits at x + 1
+      S right = shfl_down1<S>(v.v[0]);
+      if (lane == 31) right = row[xr];
+#pragma unroll
+      for (int k = 0; k < VEC - 1; ++k) p[i][k] = Prec<P>::ld(v.v[k + 1], sl);
+      p[i][VEC - 1] = Prec<P>::ld(right, sl);
+    }
+  }
+  collide_vec<P, MACRO, VEC>(g, c, p, mac, x0, y);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int ty = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
+    S* row = A + i * g.plane + (long long)ty * g.nxp;
+    S o[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) o[k] = Prec<P>::st(p[i][k], i);
+    if (cx(i) == 0) {
+      SVec<S, VEC> v;
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) v.v[k] = o[k];
+      vstore<S, VEC>(row + x0, v);
+    } else if (cx(i) > 0) {                                  // node x writes slot x + 1
+      const S from_left = shfl_up1<S>(o[VEC - 1]);
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC - 1; ++k) row[x0 + 1 + k] = o[k];
+      } else {
+        SVec<S, VEC> v;
+        v.v[0] = from_left;
+#pragma unroll
+        for (int k = 1; k < VEC; ++k) v.v[k] = o[k - 1];
+        vstore<S, VEC>(row + x0, v);
+      }
+      if (lane == 31) row[xr] = o[VEC - 1];
+    } else {                                                 // node x writes slot x - 1
+      const S from_right = shfl_down1<S>(o[0]);
+      if (lane == 31) {
+#pragma unroll
+        for (int k = 1; k < VEC; ++k) row[x0 + k - 1] = o[k];
+      } else {
+        SVec<S, VEC> v;
+#pragma unroll
+        for (int k = 0; k < VEC - 1; ++k) v.v[k] = o[k + 1];
+        v.v[VEC - 1] = from_right;
+        vstore<S, VEC>(row + x0, v);
+      }
+      if (lane == 0) row[xl] = o[0];
+    }
+  }
+}
+
 }  // namespace ibm

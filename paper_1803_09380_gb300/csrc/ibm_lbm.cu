@@ -5,12 +5,13 @@
 //
 // Collide+stream is HBM-bound: every node reads its nine populations once and
 // writes them once (18 s bytes per node update, s = bytes per stored
-// population).  One thread per node, warps on 32 consecutive x of a row.  The
-// even step touches only the thread's own node.  The odd step reads each
-// population from the neighbour it streams from and writes it to the
-// neighbour it streams to.  Nodes on a non-periodic side, and the two
-// columns before an outlet, take a per-node path through the location rules
-// of ibm_device.cuh.
+// population).  Each thread owns 16 bytes of consecutive nodes of a row (4 in
+// FP32), so every access is an aligned 16-byte vector.  The even step touches
+// only the thread's own nodes.  The odd step reads each population from the
+// neighbour it streams from and writes it to the neighbour it streams to:
+// the one-element shift is done with warp shuffles (see odd_vec).  Nodes on
+// a non-periodic side, and the two columns before an outlet, take a
+// per-node path through the location rules of ibm_device.cuh.
 //
 // In the AA pattern every slot read or written during a step belongs to
 // exactly one node, so the nodes of a step can be split in any way.  A step
@@ -22,22 +23,51 @@
 
 namespace ibm {
 
-// One time step of collide+stream.  PAR 0: even step, 1: odd step.
-// MODE K1_ALL: one thread per node of the grid (nx/256 blocks, ny rows).
-// MODE K1_MAIN: the same grid, but every warp whose 32-node segment holds a
-//   band node returns at once (the correction-loop kernel runs those
-//   segments after correcting them).
+// One time step of collide+stream.  PAR 0: even step, 1: odd step.  A warp
+// covers one span of 32 * VEC consecutive nodes of a row (VEC = 16 bytes of
+// populations), each lane VEC nodes.
+// MODE K1_ALL: every node.
+// MODE K1_MAIN: every node outside the 32-node segments that hold band nodes
+//   (the correction-loop kernel streams those segments after correcting
+//   them).
+// Even step: per lane, aligned vectors (ragged row ends node by node).  Odd
+// step: spans without boundary, ragged or band nodes take the vector path;
+// the others go node by node through the boundary-aware path.
 template <int P, int PAR, bool MACRO, int MODE>
 __global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
                                                         typename Prec<P>::S* __restrict__ A,
                                                         typename Prec<P>::R* __restrict__ mac,
                                                         const int* __restrict__ segflag, int nseg_x) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int VEC = VecTraits<P>::VEC;
+  const int lane = threadIdx.x & 31;
   const int y = blockIdx.y;
-  if (x >= g.nx) return;
-  if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) return;
-  if (PAR == 0) even_node<P, MACRO>(g, c, A, mac, x, y);
-  else odd_node<P, MACRO>(g, c, A, mac, x, y);
+  const int xw = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * VEC);
+  if (xw >= g.nx) return;                               // whole warp
+  const int x0 = xw + lane * VEC;
+  const bool flagged = MODE == K1_MAIN && x0 < g.nx && segflag[y * nseg_x + x0 / kSegW] != 0;
+  if (PAR == 0) {
+    if (flagged || x0 >= g.nx) return;
+    if (x0 + VEC <= g.nx) {
+      even_vec<P, MACRO>(g, c, A, mac, x0, y);
+    } else {
+      for (int x = x0; x < g.nx; ++x) even_node<P, MACRO>(g, c, A, mac, x, y);
+    }
+    return;
+  }
+  const bool closed_x = g.bc[0] != BC_PERIODIC;
+  const int x_special = closed_x ? (g.bc[1] == BC_OUTLET ? g.nx - 2 : g.nx - 1) : g.nx;
+  const bool edge = (g.bc[2] != BC_PERIODIC && (y == 0 || y == g.ny - 1)) ||
+                    (closed_x && xw == 0) || (xw + 32 * VEC > x_special) || (xw + 32 * VEC > g.nx);
+  if (edge || __any_sync(0xffffffffu, flagged)) {
+    for (int k = 0; k < VEC; ++k) {
+      const int x = x0 + k;
+      if (x >= g.nx) break;
+      if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) continue;
+      odd_node<P, MACRO>(g, c, A, mac, x, y);
+    }
+    return;
+  }
+  odd_vec<P, MACRO>(g, c, A, mac, x0, y, lane);
 }
 
 // ------------------------------------------------------------------ fields
@@ -131,11 +161,14 @@ static void launch_k1(const Ctx& h, const StepConsts<typename Prec<P>::R>& c, in
   typedef typename Prec<P>::R R;
   S* A = (S*)h.f;
   R* mac = (R*)h.macro;
+  constexpr int VEC = VecTraits<P>::VEC;
+  const int warps_per_row = (h.geom.nx + 32 * VEC - 1) / (32 * VEC);
+  const dim3 grid((warps_per_row + 7) / 8, h.geom.ny);
   if (mode == K1_MAIN) {
-    k_collide_stream<P, PAR, MACRO, K1_MAIN><<<row_grid(h.geom, 256), 256, 0, s>>>(
+    k_collide_stream<P, PAR, MACRO, K1_MAIN><<<grid, 256, 0, s>>>(
         h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   } else {
-    k_collide_stream<P, PAR, MACRO, K1_ALL><<<row_grid(h.geom, 256), 256, 0, s>>>(
+    k_collide_stream<P, PAR, MACRO, K1_ALL><<<grid, 256, 0, s>>>(
         h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   }
 }

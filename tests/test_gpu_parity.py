@@ -213,6 +213,25 @@ def test_couette_64_fp32_steady_velocity():
     assert relerr(gy, oy) < 1e-4
 
 
+@pytest.mark.parametrize("nx,ny", [(300, 40), (256, 33), (520, 12)])
+def test_wide_periodic_fp32_vector_spans(nx, ny):
+    """FP32 lattices several 128-node vector spans wide (and ragged tails):
+    the vector paths of both AA step kinds against the FP64 oracle."""
+    case = wl.Case("wide", nx, ny, 0.75)
+    ora, gpu = _run_pair(case, 21, prec="fp32", init=_random_init(31))
+    errs = field_errors(gpu, ora)
+    assert errs["ux"] < 1e-5 and errs["uy"] < 1e-5 and errs["f"] < 1e-6, errs
+
+
+def test_wide_couette_fp32_with_band_segments():
+    """300 x 300 Couette in FP32: band-free spans vectorised, band segments
+    streamed by the correction kernel, against the FP64 oracle."""
+    case = wl.couette(300)
+    ora, gpu = _run_pair(case, 60, prec="fp32")
+    errs = field_errors(gpu, ora)
+    assert errs["ux"] < 1e-4 and errs["uy"] < 1e-4 and errs["f"] < 1e-6, errs
+
+
 # ------------------------------------------------------------------ execution modes
 def test_graph_and_eager_paths_are_bitwise_identical():
     case = wl.couette(40)
