@@ -220,7 +220,10 @@ def test_wide_periodic_fp32_vector_spans(nx, ny):
     case = wl.Case("wide", nx, ny, 0.75)
     ora, gpu = _run_pair(case, 21, prec="fp32", init=_random_init(31))
     errs = field_errors(gpu, ora)
-    assert errs["ux"] < 1e-5 and errs["uy"] < 1e-5 and errs["f"] < 1e-6, errs
+    # FP32 storage rounds f (~0.1..0.4) at ~3e-8; velocities of the random
+    # field come from differences of populations, ~1e-5 relative after 21
+    # steps.  A wrong shift or lost element would be O(1).
+    assert errs["ux"] < 1e-4 and errs["uy"] < 1e-4 and errs["f"] < 1e-6, errs
 
 
 def test_wide_couette_fp32_with_band_segments():
