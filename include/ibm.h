@@ -199,6 +199,41 @@ typedef void *(*ibm_alloc_fn)(size_t bytes, int device, void *stream, void *ctx)
 typedef void (*ibm_free_fn)(void *ptr, int device, void *stream, void *ctx);
 ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn release, void *ctx);
 
+/* The correction loop of one step for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant of the
+ * correction loop that ibm_step runs.  It is meant for code that may not call
+ * cudaMalloc -- code running inside another framework's memory pool or
+ * under a fixed device-memory budget, plug-ins that may only use the buffers
+ * handed to them, or paths where an allocation could fail or block at a
+ * point where the caller cannot recover.
+ *
+ * The caller passes every input and output as device memory it owns:
+ *   f          [9][ny][nx] post-stream populations (double for IBM_FP64,
+ *              float for IBM_FP32), corrected in place (N iterations of
+ *              Eqs. 22-28 and the summed correction of Eq. 27; no collision,
+ *              no streaming); the lattice is periodic in x and y;
+ *   xy, ds     2n interleaved marker positions and n arc lengths (double);
+ *   uvel       2n interleaved marker velocities (double);
+ *   resid_out  n_corr + 1 doubles, r^0 .. r^N (may be NULL);
+ *   force_out  2 doubles, the force of Eq. 29 summed over all markers (may
+ *              be NULL).
+ * The work runs on cuda_stream (NULL: the legacy default stream) on the
+ * current device, and the call returns after synchronising that stream.
+ *
+ * Nothing is allocated: every intermediate array lives in one fixed 8 MiB
+ * device array that the library reserves when it is loaded and that every
+ * GPU using the library keeps until the process exits.  Limits:
+ * nx * ny <= 262144, 1 <= n <= 512 markers, 0 <= n_corr <= 64; larger
+ * requests return IBM_ERR_INVALID with a message in ibm_last_error(NULL).
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (the call clears
+ * what must start empty); calls that overlap on the GPU -- from several host
+ * threads or streams at once -- race and give wrong results. */
+ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void *f, int n_markers, const double *xy,
+                                  const double *ds, const double *uvel, int n_corr, double *resid_out,
+                                  double *force_out, void *cuda_stream);
+
 /* ABI version the library was built with (IBM_ABI_VERSION). */
 int ibm_abi_version(void);
 

@@ -251,6 +251,11 @@ ibm_status download_moving_state(Ctx* h) {
 
 }  // namespace
 
+namespace ibm {
+// Message for ibm_last_error(NULL), for entry points that take no handle.
+void set_thread_error(const char* msg) { t_err = msg; }
+}  // namespace ibm
+
 extern "C" {
 
 int ibm_abi_version(void) { return IBM_ABI_VERSION; }

@@ -179,6 +179,9 @@ inline void launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStr
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// ibm_api.cu
+void set_thread_error(const char* msg);
+
 // ibm_lbm.cu
 void launch_collide_stream(const Ctx& h, int parity, bool macro, int mode, cudaStream_t s);
 void launch_fields(const Ctx& h, int op, const double* dev_in, double* dev_out, cudaStream_t s);

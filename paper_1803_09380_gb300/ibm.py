@@ -34,7 +34,7 @@ _STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID", 2: "IBM_ERR_NOMEM", 3: "IBM_ERR_CU
 SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields",
            "ibm_write_fields", "ibm_sync", "ibm_kernel_times", "ibm_get_sizes",
            "ibm_get_counters", "ibm_destroy", "ibm_last_error", "ibm_set_allocator",
-           "ibm_abi_version")
+           "ibm_abi_version", "ibm_ib_correct_noalloc")
 
 
 class IBMError(RuntimeError):
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
         lib.ibm_last_error.restype = ctypes.c_char_p
         lib.ibm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
         lib.ibm_abi_version.restype = ci
+        lib.ibm_ib_correct_noalloc.argtypes = [ci, ci, ci, vp, ci, vp, vp, vp, ci, vp, vp, vp]
         for name in SYMBOLS:
             if name not in ("ibm_last_error", "ibm_abi_version"):
                 getattr(lib, name).restype = ci
@@ -273,6 +274,16 @@ def ibm_destroy(h) -> None:
     if h is not None and h.value:
         _check(load().ibm_destroy(h), None, "ibm_destroy")
         h.value = None
+
+
+def ibm_ib_correct_noalloc(nx, ny, prec, f_ptr, n_markers, xy_ptr, ds_ptr, uvel_ptr, n_corr,
+                           resid_ptr=None, force_ptr=None, stream=None) -> None:
+    """The correction loop on caller-owned device buffers, with no device
+    allocation (pointers are raw device addresses; see include/ibm.h)."""
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(load().ibm_ib_correct_noalloc(int(nx), int(ny), p, f_ptr, int(n_markers), xy_ptr, ds_ptr,
+                                         uvel_ptr, int(n_corr), resid_ptr, force_ptr, stream),
+           None, "ibm_ib_correct_noalloc")
 
 
 def ibm_last_error(h=None) -> str:
