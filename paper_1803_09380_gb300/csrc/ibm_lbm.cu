@@ -5,12 +5,13 @@
 //
 // Collide+stream is HBM-bound: every node reads its nine populations once and
 // writes them once (18 s bytes per node update, s = bytes per stored
-// population).  Global accesses are aligned 16-byte vectors.  The even step
-// touches only the thread's own nodes.  The odd step reads each population
-// from the neighbour it streams from and writes it to the neighbour it
-// streams to: the one-element shift goes through shared memory (see k_odd).
-// Nodes on a non-periodic side, and the two columns before an outlet, take
-// a per-node path through the location rules of ibm_device.cuh.
+// population).  Each thread owns 16 bytes of consecutive nodes of a row (4 in
+// FP32), so every access is an aligned 16-byte vector.  The even step touches
+// only the thread's own nodes.  The odd step reads each population from the
+// neighbour it streams from and writes it to the neighbour it streams to:
+// the one-element shift is done with warp shuffles (see odd_vec).  Nodes on
+// a non-periodic side, and the two columns before an outlet, take a
+// per-node path through the location rules of ibm_device.cuh.
 //
 // In the AA pattern every slot read or written during a step belongs to
 // exactly one node, so the nodes of a step can be split in any way.  A step
@@ -22,138 +23,51 @@
 
 namespace ibm {
 
-// Even step of collide+stream: each lane owns VEC consecutive nodes (16
-// bytes of populations) and moves them with aligned vectors; ragged row ends
-// go node by node.
+// One time step of collide+stream.  PAR 0: even step, 1: odd step.  A warp
+// covers one span of 32 * VEC consecutive nodes of a row (VEC = 16 bytes of
+// populations), each lane VEC nodes.
 // MODE K1_ALL: every node.
 // MODE K1_MAIN: every node outside the 32-node segments that hold band nodes
 //   (the correction-loop kernel streams those segments after correcting
 //   them).
-template <int P, bool MACRO, int MODE>
-__global__ void __launch_bounds__(256) k_even(Geom g, StepConsts<typename Prec<P>::R> c,
-                                              typename Prec<P>::S* __restrict__ A,
-                                              typename Prec<P>::R* __restrict__ mac,
-                                              const int* __restrict__ segflag, int nseg_x) {
+// Even step: per lane, aligned vectors (ragged row ends node by node).  Odd
+// step: spans without boundary, ragged or band nodes take the vector path;
+// the others go node by node through the boundary-aware path.
+template <int P, int PAR, bool MACRO, int MODE>
+__global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
+                                                        typename Prec<P>::S* __restrict__ A,
+                                                        typename Prec<P>::R* __restrict__ mac,
+                                                        const int* __restrict__ segflag, int nseg_x) {
   constexpr int VEC = VecTraits<P>::VEC;
+  const int lane = threadIdx.x & 31;
   const int y = blockIdx.y;
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
-  if (x0 >= g.nx) return;
-  if (MODE == K1_MAIN && segflag[y * nseg_x + x0 / kSegW] != 0) return;
-  if (x0 + VEC <= g.nx) {
-    even_vec<P, MACRO>(g, c, A, mac, x0, y);
-  } else {
-    for (int x = x0; x < g.nx; ++x) even_node<P, MACRO>(g, c, A, mac, x, y);
+  const int xw = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * VEC);
+  if (xw >= g.nx) return;                               // whole warp
+  const int x0 = xw + lane * VEC;
+  const bool flagged = MODE == K1_MAIN && x0 < g.nx && segflag[y * nseg_x + x0 / kSegW] != 0;
+  if (PAR == 0) {
+    if (flagged || x0 >= g.nx) return;
+    if (x0 + VEC <= g.nx) {
+      even_vec<P, MACRO>(g, c, A, mac, x0, y);
+    } else {
+      for (int x = x0; x < g.nx; ++x) even_node<P, MACRO>(g, c, A, mac, x, y);
+    }
+    return;
   }
-}
-
-// Odd step of collide+stream through shared memory.  A block owns a run of
-// B = kOddThreads * VEC consecutive nodes of one row.
-//   1. For each population, the aligned source run of its row is loaded with
-//      16-byte vectors into shared memory, plus the one halo element the run
-//      needs from outside (read by the thread of the node that owns it).
-//   2. Each node reads its nine incoming populations from shared memory
-//      (consecutive threads, consecutive nodes), collides, and writes the
-//      nine outgoing ones to a second shared buffer at their target
-//      positions.
-//   3. Each target run is stored with 16-byte vectors; an element whose
-//      owning node is not handled by this pass (another block's node, a
-//      band node, a boundary node) is left alone, or written by its owner
-//      as a scalar (the one halo element per direction).
-// Boundary nodes (closed sides, the two columns before an outlet) then run
-// the per-node boundary path; in the AA pattern every slot belongs to one
-// node, so none of these writes overlap.  Boundary rows of a closed y axis
-// and ragged row ends go node by node.
-constexpr int kOddThreads = 128;
-
-template <int P, bool MACRO, int MODE>
-__global__ void __launch_bounds__(kOddThreads) k_odd(Geom g, StepConsts<typename Prec<P>::R> c,
-                                                     typename Prec<P>::S* __restrict__ A,
-                                                     typename Prec<P>::R* __restrict__ mac,
-                                                     const int* __restrict__ segflag, int nseg_x) {
-  typedef typename Prec<P>::S S;
-  typedef typename Prec<P>::R R;
-  constexpr int VEC = VecTraits<P>::VEC;
-  constexpr int B = kOddThreads * VEC;
-  constexpr int W = B + 2 * VEC;                    // run plus one vector of halo each side
-  __shared__ __align__(16) S bin[9][W];
-  __shared__ __align__(16) S bout[9][W];
-  __shared__ unsigned char kind[B];                 // 0 vector pass, 1 boundary path, 2 skip (band)
-  const int t = threadIdx.x;
-  const int y = blockIdx.y;
-  const int xb = blockIdx.x * B;
-  if (xb >= g.nx) return;
   const bool closed_x = g.bc[0] != BC_PERIODIC;
-  const bool row_edge = g.bc[2] != BC_PERIODIC && (y == 0 || y == g.ny - 1);
-  if (row_edge || xb + B > g.nx) {                  // node by node
+  const int x_special = closed_x ? (g.bc[1] == BC_OUTLET ? g.nx - 2 : g.nx - 1) : g.nx;
+  const bool edge = (g.bc[2] != BC_PERIODIC && (y == 0 || y == g.ny - 1)) ||
+                    (closed_x && xw == 0) || (xw + 32 * VEC > x_special) || (xw + 32 * VEC > g.nx);
+  if (edge || __any_sync(0xffffffffu, flagged)) {
     for (int k = 0; k < VEC; ++k) {
-      const int x = xb + t + k * kOddThreads;
+      const int x = x0 + k;
       if (x >= g.nx) break;
       if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) continue;
       odd_node<P, MACRO>(g, c, A, mac, x, y);
     }
     return;
   }
-  for (int k = 0; k < VEC; ++k) {
-    const int n = t + k * kOddThreads, x = xb + n;
-    unsigned char q = needs_boundary_path(g, x, y) ? 1 : 0;
-    if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) q = 2;
-    kind[n] = q;
-  }
-  const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-  const int xl = xb == 0 ? (closed_x ? -1 : g.nx - 1) : xb - 1;          // left halo column
-  const int xr = xb + B == g.nx ? (closed_x ? -1 : 0) : xb + B;          // right halo column
-  // 1. loads
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int sy = cy(i) > 0 ? ym : (cy(i) < 0 ? yp : y);
-    const S* row = A + opp(i) * g.plane + (long long)sy * g.nxp;
-    vstore<S, VEC>(&bin[i][VEC + t * VEC], vload<S, VEC>(row + xb + t * VEC));
-    if (cx(i) > 0 && t == 0 && xl >= 0) bin[i][VEC - 1] = row[xl];
-    if (cx(i) < 0 && t == kOddThreads - 1 && xr >= 0) bin[i][VEC + B] = row[xr];
-  }
-  __syncthreads();
-  // 2. collide every node of the vector pass
-  for (int k = 0; k < VEC; ++k) {
-    const int n = t + k * kOddThreads;
-    if (kind[n] != 0) continue;
-    R p[9], ps[9], rho, jx, jy;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) p[i] = Prec<P>::ld(bin[i][VEC + n - cx(i)], opp(i));
-    bgk<R>(p, ps, rho, jx, jy, c.omega);
-    if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + xb + n, rho, jx, jy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) bout[i][VEC + n + cx(i)] = Prec<P>::st(ps[i], i);
-  }
-  __syncthreads();
-  // 3. stores: element p (run position) of population i belongs to node p - cx(i)
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int ty = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
-    S* row = A + i * g.plane + (long long)ty * g.nxp;
-    const int p0 = t * VEC;
-    bool all = true;
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      const int m = p0 + k - cx(i);
-      all = all && m >= 0 && m < B && kind[m] == 0;
-    }
-    if (all) {
-      vstore<S, VEC>(row + xb + p0, *reinterpret_cast<const SVec<S, VEC>*>(&bout[i][VEC + p0]));
-    } else {
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        const int m = p0 + k - cx(i);
-        if (m >= 0 && m < B && kind[m] == 0) row[xb + p0 + k] = bout[i][VEC + p0 + k];
-      }
-    }
-    if (cx(i) > 0 && t == kOddThreads - 1 && kind[B - 1] == 0 && xr >= 0) row[xr] = bout[i][VEC + B];
-    if (cx(i) < 0 && t == 0 && kind[0] == 0 && xl >= 0) row[xl] = bout[i][VEC - 1];
-  }
-  // boundary nodes of this run
-  for (int k = 0; k < VEC; ++k) {
-    const int n = t + k * kOddThreads;
-    if (kind[n] == 1) odd_node<P, MACRO>(g, c, A, mac, xb + n, y);
-  }
+  odd_vec<P, MACRO>(g, c, A, mac, x0, y, lane);
 }
 
 // ------------------------------------------------------------------ fields
@@ -248,20 +162,14 @@ static void launch_k1(const Ctx& h, const StepConsts<typename Prec<P>::R>& c, in
   S* A = (S*)h.f;
   R* mac = (R*)h.macro;
   constexpr int VEC = VecTraits<P>::VEC;
-  if (PAR == 0) {
-    const int lanes = (h.geom.nx + VEC - 1) / VEC;
-    const dim3 grid((lanes + 255) / 256, h.geom.ny);
-    if (mode == K1_MAIN)
-      k_even<P, MACRO, K1_MAIN><<<grid, 256, 0, s>>>(h.geom, c, A, mac, h.dsegflag, h.nseg_x);
-    else
-      k_even<P, MACRO, K1_ALL><<<grid, 256, 0, s>>>(h.geom, c, A, mac, h.dsegflag, h.nseg_x);
+  const int warps_per_row = (h.geom.nx + 32 * VEC - 1) / (32 * VEC);
+  const dim3 grid((warps_per_row + 7) / 8, h.geom.ny);
+  if (mode == K1_MAIN) {
+    k_collide_stream<P, PAR, MACRO, K1_MAIN><<<grid, 256, 0, s>>>(
+        h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   } else {
-    constexpr int B = kOddThreads * VEC;
-    const dim3 grid((h.geom.nx + B - 1) / B, h.geom.ny);
-    if (mode == K1_MAIN)
-      k_odd<P, MACRO, K1_MAIN><<<grid, kOddThreads, 0, s>>>(h.geom, c, A, mac, h.dsegflag, h.nseg_x);
-    else
-      k_odd<P, MACRO, K1_ALL><<<grid, kOddThreads, 0, s>>>(h.geom, c, A, mac, h.dsegflag, h.nseg_x);
+    k_collide_stream<P, PAR, MACRO, K1_ALL><<<grid, 256, 0, s>>>(
+        h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   }
 }
 
