@@ -226,6 +226,43 @@ def test_wide_periodic_fp32_vector_spans(nx, ny):
     assert errs["ux"] < 1e-4 and errs["uy"] < 1e-4 and errs["f"] < 1e-6, errs
 
 
+def test_wide_fp32_periodic_many_spans():
+    """FP32, 1100 nodes wide: eight full 128-node vector spans and a ragged
+    tail, against the FP64 oracle."""
+    case = wl.Case("blocks", 1100, 24, 0.7)
+    ora, gpu = _run_pair(case, 21, prec="fp32", init=_random_init(41))
+    errs = field_errors(gpu, ora)
+    assert errs["ux"] < 1e-4 and errs["uy"] < 1e-4 and errs["f"] < 1e-6, errs
+
+
+def test_wide_fp64_box_walls():
+    """FP64, 512 x 20 box (eight 64-node vector spans per row): bounce-back
+    sides, a moving lid, closed rows and columns."""
+    wall_u = np.zeros(8)
+    wall_u[6] = 0.02
+    case = wl.Case("box512", 512, 20, 0.8, bc=(1, 1, 1, 1), wall_u=tuple(wall_u))
+    ora, gpu = _run_pair(case, 30, init=_random_init(43))
+    _assert_fields(gpu, ora, TOL64)
+
+
+def test_wide_fp32_channel():
+    """FP32 channel 1024 x 40: equilibrium inlet, zero-gradient outlet,
+    free-slip walls, a cylinder; full vector spans between the edges."""
+    case = wl.cylinder(nx=1024, ny=40, diameter=10.0, center=(200.0, 19.7), u_in=0.05, re=20.0,
+                       markers=31)
+    ora, gpu = _run_pair(case, 40, prec="fp32")
+    errs = field_errors(gpu, ora)
+    assert errs["ux"] < 1e-4 and errs["uy"] < 1e-4 and errs["f"] < 1e-6, errs
+
+
+def test_couette_520_fp64_band_flags_in_spans():
+    """FP64 Couette 520^2: band segments next to full vector spans."""
+    case = wl.couette(520)
+    ora, gpu = _run_pair(case, 6)
+    _assert_fields(gpu, ora, TOL64)
+    assert relerr(gpu.resid, ora.resid) < 1e-10
+
+
 def test_wide_couette_fp32_with_band_segments():
     """300 x 300 Couette in FP32: band-free spans vectorised, band segments
     streamed by the correction kernel, against the FP64 oracle."""
