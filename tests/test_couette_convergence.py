@@ -1,0 +1,83 @@
+"""Cylindrical Couette flow (section 3.1.2): convergence of the steady state
+to the analytic profile of Eq. 34 under grid refinement.
+
+The stored sweep (tests/golden/couette_sweep.json) was written by
+tests/golden/make_couette_sweep.py, which calls only the oracle.  Under the
+sweep's scaling (radii 0.156 N and 0.39 N, wall speed and tau fixed) the
+method converges at first order in the relative L2 norm: the diffuse
+interface places the effective wall off the marker ring by a fraction of
+a lattice spacing.  The pins: the error falls monotonically, with slope
+<= -0.9, and the stored values are reproduced by the current oracle."""
+import json
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden", "couette_sweep.json")
+sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+
+import oracle  # noqa: E402
+from paper_1803_09380_gb300 import workloads as wl  # noqa: E402
+
+
+def load():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def rel_l2(case, ux, uy):
+    m = case.meta
+    y, x = np.mgrid[0:case.ny, 0:case.nx].astype(np.float64)
+    ax, ay = wl.couette_analytic(case, x, y)
+    r = np.hypot(x - m["cx"], y - m["cy"])
+    ann = (r >= m["r1"]) & (r <= m["r2"])
+    return math.sqrt(((ux - ax) ** 2 + (uy - ay) ** 2)[ann].sum() / (ax ** 2 + ay ** 2)[ann].sum())
+
+
+def test_stored_sweep_converges_to_the_analytic_profile():
+    doc = load()
+    runs = doc["runs"]
+    errs = [r["rel_l2_annulus"] for r in runs]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert doc["slope_rel_l2_annulus"] <= -0.9
+    assert doc["slope_l2_profile"] <= -0.9
+    assert errs[-1] < 0.04
+
+
+def test_stored_sweep_matches_the_current_oracle():
+    """Recompute the coarsest entry: the stored numbers are the oracle's."""
+    run = load()["runs"][0]
+    case = wl.couette(run["n"])
+    L = oracle.Lattice(case.nx, case.ny, case.tau, n_corr=case.n_corr)
+    for b in case.bodies:
+        L.add_body(b.xy, b.ds, **b.as_kwargs())
+    L.step(run["steps"])
+    _, ux, uy = L.moments()
+    assert abs(rel_l2(case, ux, uy) - run["rel_l2_annulus"]) < 1e-9 * run["rel_l2_annulus"]
+
+
+@pytest.mark.gpu
+def test_fp32_gpu_keeps_the_oracle_errors_and_slope():
+    """FP32 on the GPU, same sizes and step counts as the FP64 oracle sweep
+    (N <= 128), plus N = 256: every error within 1e-3 relative of the
+    oracle's and the same first-order slope."""
+    from paper_1803_09380_gb300 import ibm
+    runs = [r for r in load()["runs"] if r["n"] <= 128]
+    ns, errs = [], []
+    for r in runs + [{"n": 256, "steps": 4 * 20500}]:
+        case = wl.couette(r["n"])
+        lat = ibm.Lattice.from_case(case, prec="fp32")
+        lat.step(r["steps"])
+        _, ux, uy = lat.moments()
+        e = rel_l2(case, ux, uy)
+        lat.close()
+        if "rel_l2_annulus" in r:
+            assert abs(e - r["rel_l2_annulus"]) < 1e-3 * r["rel_l2_annulus"]
+        ns.append(r["n"])
+        errs.append(e)
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert abs(slope - load()["slope_rel_l2_annulus"]) < 0.05
