@@ -262,10 +262,18 @@ struct IbArgs {
 // 64-bit arrival counter only grows: the k-th barrier of all launches is
 // complete when it reaches k * gridDim.x.  The wait is bounded: after
 // kBarrierCycles the CTA records ERR_BARRIER and goes on, so a broken launch
-// ends with an error status instead of hanging.
-__device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr) {
+// ends with an error status instead of hanging.  When dst is given, the
+// per-warp maxima in red[] are combined first and folded into *dst.
+template <class R>
+__device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr, const R* red = nullptr,
+                                             R* dst = nullptr) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (dst) {
+      R m = red[0];
+      for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
+      if (m > R(0) || m != m) AtomicBits<R>::max(dst, m);
+    }
     __threadfence();
     const unsigned long long g = gridDim.x;
     const unsigned long long t = atomicAdd(bar, 1ull) + 1ull;
@@ -280,31 +288,29 @@ __device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr) 
   __syncthreads();
 }
 
+// Warp maximum of v into red[warp] (read by grid_barrier).
 template <class R>
-__device__ __forceinline__ void block_max_to(R v, R* dst) {
-  __shared__ R red[kIbThreads / 32];
+__device__ __forceinline__ void warp_max_to(R v, R* red) {
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R m = red[0];
-    for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
-    if (m > R(0) || m != m) AtomicBits<R>::max(dst, m);
-  }
-  __syncthreads();
 }
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int h = kIbThreads / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-    __syncthreads();
+// Block sums of three doubles with a fixed-shape reduction (warp butterfly,
+// then the warp totals in warp order).
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    c += __shfl_xor_sync(0xffffffffu, c, off);
   }
-  const double r = sh[0];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sh[w] = a; sh[8 + w] = b; sh[16 + w] = c; }
   __syncthreads();
-  return r;
+  a = sh[0]; b = sh[8]; c = sh[16];
+  for (int k = 1; k < kIbThreads / 32; ++k) { a += sh[k]; b += sh[8 + k]; c += sh[16 + k]; }
+  __syncthreads();
 }
 
 template <class R> struct Vec2;
@@ -372,11 +378,40 @@ __device__ __forceinline__ void deviation(const Args& a, int l, const R* __restr
   djy = a.mq[4 * l + 2] - sy;
 }
 
-template <int P, int PAR, bool MACRO>
+// Band-node part of an iteration phase: j^n(x) = j^0(x) + sum_m W_m ds_m A^n_m
+// and its contribution j^n j^n to S2 (bq[3..5]); with last = true the
+// spread of A^N itself (bq[6..7]).
+template <class R>
+__device__ __forceinline__ void band_history(R* __restrict__ bq, const Ent<R>* __restrict__ ent,
+                                             const int* __restrict__ bcnt, const R* __restrict__ An,
+                                             int b, bool first, bool last) {
+  R px = R(0), py = R(0);
+  if (!first) row_dot<R>(ent + (long long)b * kBandCap, bcnt + b, An, 0, px, py);
+  if (last) {
+    bq[8 * b + 6] = px;
+    bq[8 * b + 7] = py;
+    return;
+  }
+  const R jx = bq[8 * b + 1] + px, jy = bq[8 * b + 2] + py;
+  if (first) {
+    bq[8 * b + 3] = jx * jx;
+    bq[8 * b + 4] = jx * jy;
+    bq[8 * b + 5] = jy * jy;
+  } else {
+    bq[8 * b + 3] += jx * jx;
+    bq[8 * b + 4] += jx * jy;
+    bq[8 * b + 5] += jy * jy;
+  }
+}
+
+template <int P, int PAR>
 __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
   typedef typename Prec<P>::R R;
+  __shared__ R red[kIbThreads / 32];
+  __shared__ double sh[24];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
+  const int rtid = nth - 1 - tid;                  // band work starts from the other end
   const int nband = min(a.ctr[CTR_NBAND], a.bcap);
   const int M = a.M, N = a.N;
   long long where;
@@ -393,10 +428,10 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
     a.bq[8 * b + 1] = jx;
     a.bq[8 * b + 2] = jy;
   }
-  grid_barrier(a.bar, a.ctr);
+  grid_barrier<R>(a.bar, a.ctr);
 
-  // interpolate rho*, J*^0 (Eq. 22b with Eq. 28 in moment form), b_l, and
-  // iteration 0 (A^0 = 0, so dj^0 = b)
+  // phase 0: interpolate rho*, J*^0 (Eq. 22b with Eq. 28 in moment form),
+  // b_l = rho* U_l - J*^0 and A^1 = b (A^0 = 0); band nodes: S2 = j^0 j^0
   {
     R rmax = R(0);
     for (int l = tid; l < M; l += nth) {
@@ -427,11 +462,14 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       }
       rmax = nanmax(rmax, (R)(sqrt(bx * bx + by * by) / rs));
     }
-    block_max_to<R>(rmax, a.resid);
+    if (N > 0)
+      for (int b = rtid; b < nband; b += nth) band_history<R>(a.bq, a.ent, a.bcnt, nullptr, b, true, false);
+    warp_max_to<R>(rmax, red);
   }
-  grid_barrier(a.bar, a.ctr);
+  grid_barrier<R>(a.bar, a.ctr, red, a.resid);
 
-  // iterations 1..N-1 (Jacobi: read A^n, write A^{n+1})
+  // phases 1..N-1: Jacobi iteration A^{n+1} = A^n + b - G A^n; band nodes
+  // add j^n j^n to S2
   for (int n = 1; n < N; ++n) {
     const R* An = a.Ah + (long long)n * 2 * M;
     R* An1 = a.Ah + (long long)(n + 1) * 2 * M;
@@ -443,65 +481,28 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       An1[2 * l + 1] = An[2 * l + 1] + djy;
       rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
     }
-    block_max_to<R>(rmax, a.resid + n);
-    grid_barrier(a.bar, a.ctr);
+    for (int b = rtid; b < nband; b += nth) band_history<R>(a.bq, a.ent, a.bcnt, An, b, false, false);
+    warp_max_to<R>(rmax, red);
+    grid_barrier<R>(a.bar, a.ctr, red, a.resid + n);
   }
 
-  // final residual r^N, and per band node the final spread D^N and
-  // sum_n j^n j^n over the iterations
+  // final phase: residual r^N; band nodes keep the spread of A^N
+  const R* AN = a.Ah + (long long)N * 2 * M;
   {
-    const R* AN = a.Ah + (long long)N * 2 * M;
     R rmax = R(0);
     for (int l = tid; l < M; l += nth) {
       R djx, djy;
       deviation<R>(a, l, AN, djx, djy);
       rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
     }
-    block_max_to<R>(rmax, a.resid + N);
+    if (N > 0)
+      for (int b = rtid; b < nband; b += nth) band_history<R>(a.bq, a.ent, a.bcnt, AN, b, false, true);
+    warp_max_to<R>(rmax, red);
   }
-  if (N > 0) {
-    typedef typename Vec2<R>::T V;
-    for (int b = tid; b < nband; b += nth) {
-      const R j0x = a.bq[8 * b + 1], j0y = a.bq[8 * b + 2];
-      const Ent<R>* e = a.ent + (long long)b * kBandCap;
-      Ent<R> q[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) q[j] = e[j];
-      const int cnt = a.bcnt[b];
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (j >= cnt) { q[j].m = 0; q[j].w = R(0); }
-      R sxx = R(0), sxy = R(0), syy = R(0), dx = R(0), dy = R(0);
-#pragma unroll 4
-      for (int n = 0; n <= N; ++n) {
-        const V* Av = reinterpret_cast<const V*>(a.Ah + (long long)n * 2 * M);
-        V v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = Av[q[j].m];
-        R px = R(0), py = R(0);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          px += q[j].w * v[j].x;
-          py += q[j].w * v[j].y;
-        }
-        if (cnt > 8) sparse_dot<R>(e + 8, cnt - 8, a.Ah + (long long)n * 2 * M, 0, px, py);
-        if (n < N) {
-          const R jx = j0x + px, jy = j0y + py;
-          sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
-        } else {
-          dx = px; dy = py;
-        }
-      }
-      a.bq[8 * b + 3] = sxx;
-      a.bq[8 * b + 4] = sxy;
-      a.bq[8 * b + 5] = syy;
-      a.bq[8 * b + 6] = dx;
-      a.bq[8 * b + 7] = dy;
-    }
-  }
-  grid_barrier(a.bar, a.ctr);
+  grid_barrier<R>(a.bar, a.ctr, red, a.resid + N);
 
-  // second-moment deviations summed over the iterations
+  // second-moment deviations summed over the iterations:
+  // C_l = N rho* U U - sum_x W_l(x) / rho(x) sum_n j^n j^n
   if (N > 0) {
     for (int l = tid; l < M; l += nth) {
       R pxx = R(0), pxy = R(0), pyy = R(0);
@@ -526,10 +527,9 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       a.Cm[3 * l + 2] = R(N) * rs * uy * uy - pyy;
     }
   }
-  grid_barrier(a.bar, a.ctr);
+  grid_barrier<R>(a.bar, a.ctr);
 
   // Eq. 27 summed over the iterations: f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi]
-  const R* AN = a.Ah + (long long)N * 2 * M;
   if (N > 0) {
     for (int b = tid; b < nband; b += nth) {
       R pxx = R(0), pxy = R(0), pyy = R(0);
@@ -572,7 +572,6 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
 
   // Eq. 29: per-CTA partial force and torque of each body over a fixed
   // chunk of markers, F_l = -ds_l A^N_l, T_l = (X_l - x_c) x F_l (FP64).
-  __shared__ double sh[kIbThreads];
   const int chunk = (M + gridDim.x - 1) / gridDim.x;
   const int lo = blockIdx.x * chunk, hi = min(M, lo + chunk);
   if (a.nb > 0 && lo < hi) {
@@ -587,46 +586,50 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
         fy += Fy;
         tq += (a.X[l] - B.xc[0]) * Fy - (a.Y[l] - B.xc[1]) * Fx;
       }
-      fx = block_sum(fx, sh);
-      fy = block_sum(fy, sh);
-      tq = block_sum(tq, sh);
+      block_sum3(fx, fy, tq, sh);
       if (threadIdx.x == 0) {
         double* o = a.fpart + ((long long)blockIdx.x * a.nb + bd) * 3;
         o[0] = fx; o[1] = fy; o[2] = tq;
       }
     }
   }
-  grid_barrier(a.bar, a.ctr);
-
-  // collide+stream of the band row segments
-  {
-    const int nseg = a.ctr[CTR_NSEG];
-    const int lane = threadIdx.x & (kSegW - 1);
-    for (int k = tid / kSegW; k < nseg; k += nth / kSegW) {
-      const int seg = a.seglist[k];
-      const int y = seg / a.nseg_x, x = (seg % a.nseg_x) * kSegW + lane;
-      if (x >= a.g.nx) continue;
-      if (PAR == 0) even_node<P, MACRO>(a.g, a.c, a.A, a.mac, x, y);
-      else odd_node<P, MACRO>(a.g, a.c, a.A, a.mac, x, y);
-    }
-  }
+  grid_barrier<R>(a.bar, a.ctr);
 
   // body totals: one body per CTA, fixed-shape reduction over the chunks
   for (int bd = blockIdx.x; bd < a.nb; bd += gridDim.x) {
     BodyDev& B = a.bodies[bd];
     const int k0 = B.m0 / chunk, k1 = (B.m1 - 1) / chunk;
-    double f[3];
-    for (int q = 0; q < 3; ++q) {
-      double v = 0.0;
-      for (int k = k0 + (int)threadIdx.x; k <= k1; k += blockDim.x)
-        v += a.fpart[((long long)k * a.nb + bd) * 3 + q];
-      f[q] = block_sum(v, sh);
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    for (int k = k0 + (int)threadIdx.x; k <= k1; k += blockDim.x) {
+      const double* o = a.fpart + ((long long)k * a.nb + bd) * 3;
+      f0 += o[0]; f1 += o[1]; f2 += o[2];
     }
+    block_sum3(f0, f1, f2, sh);
     if (threadIdx.x == 0) {
-      B.F_ib[0] = f[0];
-      B.F_ib[1] = f[1];
-      B.T_ib = f[2];
+      B.F_ib[0] = f0;
+      B.F_ib[1] = f1;
+      B.T_ib = f2;
     }
+  }
+}
+
+// Collide+stream of the 32-node row segments that hold band nodes, after
+// the correction kernel has corrected them: one warp per segment.
+template <int P, int PAR, bool MACRO>
+__global__ void __launch_bounds__(256) k_band_collide(Geom g, StepConsts<typename Prec<P>::R> c,
+                                                      typename Prec<P>::S* __restrict__ A,
+                                                      typename Prec<P>::R* __restrict__ mac,
+                                                      const int* __restrict__ seglist,
+                                                      const int* __restrict__ ctr, int nseg_x) {
+  const int nseg = ctr[CTR_NSEG];
+  const int lane = threadIdx.x & (kSegW - 1);
+  const int nw = (gridDim.x * blockDim.x) / kSegW;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / kSegW; k < nseg; k += nw) {
+    const int seg = seglist[k];
+    const int y = seg / nseg_x, x = (seg % nseg_x) * kSegW + lane;
+    if (x >= g.nx) continue;
+    if (PAR == 0) even_node<P, MACRO>(g, c, A, mac, x, y);
+    else odd_node<P, MACRO>(g, c, A, mac, x, y);
   }
 }
 
@@ -779,12 +782,20 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   a.bar = h.dbar;
   cudaMemsetAsync(h.dresid, 0, sizeof(R) * (a.N + 1), s);
   const dim3 grid(h.ib_grid), block(kIbThreads);
-  if (parity == 0) {
-    if (macro) launch_prio(k_ib_step<P, 0, true>, grid, block, s, h.ib_prio, a);
-    else launch_prio(k_ib_step<P, 0, false>, grid, block, s, h.ib_prio, a);
-  } else {
-    if (macro) launch_prio(k_ib_step<P, 1, true>, grid, block, s, h.ib_prio, a);
-    else launch_prio(k_ib_step<P, 1, false>, grid, block, s, h.ib_prio, a);
+  if (parity == 0) launch_prio(k_ib_step<P, 0>, grid, block, s, h.ib_prio, a);
+  else launch_prio(k_ib_step<P, 1>, grid, block, s, h.ib_prio, a);
+  // the band segments, once corrected
+  if (h.band_collide) {
+    const int need = (h.segcap * kSegW + 255) / 256;
+    const dim3 g2(need < 8 * h.ib_grid ? (need > 0 ? need : 1) : 8 * h.ib_grid), b2(256);
+    const int* ctr = a.ctr;
+    if (parity == 0) {
+      if (macro) launch_prio(k_band_collide<P, 0, true>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+      else launch_prio(k_band_collide<P, 0, false>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+    } else {
+      if (macro) launch_prio(k_band_collide<P, 1, true>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+      else launch_prio(k_band_collide<P, 1, false>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+    }
   }
 }
 
@@ -802,8 +813,8 @@ void launch_ib_loop(const Ctx& h, int parity, bool macro, cudaStream_t s) {
 template <int P>
 static int ib_blocks_per_sm_t() {
   int n0 = 0, n1 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ib_step<P, 0, true>, kIbThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ib_step<P, 1, true>, kIbThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ib_step<P, 0>, kIbThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ib_step<P, 1>, kIbThreads, 0);
   return n0 < n1 ? n0 : n1;
 }
 

@@ -106,6 +106,7 @@ struct Ctx {
   double* dfpart = nullptr;                  // [ib_grid][nb][3] force partial sums
   unsigned long long* dbar = nullptr;        // grid-barrier arrivals of the correction kernel
   int ib_grid = 0;                           // CTAs of the correction kernel (one per SM)
+  bool band_collide = true;                  // stream the band segments after the correction
   bool band_valid = false;
 
   // CUDA graphs of one step, per parity and macro flag
@@ -135,7 +136,7 @@ inline int kernels_per_step(const Ctx& h) {
   if (h.nm > 0) {
     const int N = h.desc.n_corr;
     (void)N;
-    k += 1;                                        // correction loop (+ band collide+stream)
+    k += 2;                                        // correction loop, band collide+stream
     if (h.nb > 0 && h.any_moving) k += 2 + 6;      // body update, marker move, band rebuild
   }
   return k;

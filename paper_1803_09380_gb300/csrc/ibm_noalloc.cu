@@ -169,6 +169,7 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
   c.segcap = c.bcap;
   c.ib_grid = sms;
   c.ib_prio = 0;
+  c.band_collide = false;                   // correction only
   const size_t R = c.r_bytes;
   const size_t ent_bytes = prec == IBM_FP64 ? sizeof(Ent<double>) : sizeof(Ent<float>);
   const long long nodes = (long long)nx * ny;
@@ -221,8 +222,6 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
     k_na_prepare<float><<<(n_markers + 127) / 128, 128, 0, s>>>(n_markers, xy, ds, uvel, c.dX, c.dY, c.dds,
         c.ddX, c.ddY, c.dmbody, (float*)c.dUx, (float*)c.dUy, c.dbodies);
   launch_band_build(c, s);
-  // correction only: no band segments to stream
-  cudaMemsetAsync(c.dctr + CTR_NSEG, 0, sizeof(int), s);
   launch_ib_loop(c, 0, false, s);
   if (prec == IBM_FP64)
     k_na_finish<double><<<1, 128, 0, s>>>(n_corr + 1, (const double*)c.dresid, c.dbodies, resid_out, force_out);
