@@ -378,32 +378,6 @@ __device__ __forceinline__ void deviation(const Args& a, int l, const R* __restr
   djy = a.mq[4 * l + 2] - sy;
 }
 
-// Band-node part of an iteration phase: j^n(x) = j^0(x) + sum_m W_m ds_m A^n_m
-// and its contribution j^n j^n to S2 (bq[3..5]); with last = true the
-// spread of A^N itself (bq[6..7]).
-template <class R>
-__device__ __forceinline__ void band_history(R* __restrict__ bq, const Ent<R>* __restrict__ ent,
-                                             const int* __restrict__ bcnt, const R* __restrict__ An,
-                                             int b, bool first, bool last) {
-  R px = R(0), py = R(0);
-  if (!first) row_dot<R>(ent + (long long)b * kBandCap, bcnt + b, An, 0, px, py);
-  if (last) {
-    bq[8 * b + 6] = px;
-    bq[8 * b + 7] = py;
-    return;
-  }
-  const R jx = bq[8 * b + 1] + px, jy = bq[8 * b + 2] + py;
-  if (first) {
-    bq[8 * b + 3] = jx * jx;
-    bq[8 * b + 4] = jx * jy;
-    bq[8 * b + 5] = jy * jy;
-  } else {
-    bq[8 * b + 3] += jx * jx;
-    bq[8 * b + 4] += jx * jy;
-    bq[8 * b + 5] += jy * jy;
-  }
-}
-
 template <int P, int PAR>
 __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
   typedef typename Prec<P>::R R;
@@ -462,8 +436,6 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       }
       rmax = nanmax(rmax, (R)(sqrt(bx * bx + by * by) / rs));
     }
-    if (N > 0)
-      for (int b = rtid; b < nband; b += nth) band_history<R>(a.bq, a.ent, a.bcnt, nullptr, b, true, false);
     warp_max_to<R>(rmax, red);
   }
   grid_barrier<R>(a.bar, a.ctr, red, a.resid);
@@ -481,12 +453,13 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       An1[2 * l + 1] = An[2 * l + 1] + djy;
       rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
     }
-    for (int b = rtid; b < nband; b += nth) band_history<R>(a.bq, a.ent, a.bcnt, An, b, false, false);
     warp_max_to<R>(rmax, red);
     grid_barrier<R>(a.bar, a.ctr, red, a.resid + n);
   }
 
-  // final phase: residual r^N; band nodes keep the spread of A^N
+  // final phase: residual r^N; per band node the final spread D^N and
+  // sum_n j^n j^n over the iterations (entries gathered once, then every
+  // A^n read eight at a time)
   const R* AN = a.Ah + (long long)N * 2 * M;
   {
     R rmax = R(0);
@@ -495,9 +468,47 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
       deviation<R>(a, l, AN, djx, djy);
       rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
     }
-    if (N > 0)
-      for (int b = rtid; b < nband; b += nth) band_history<R>(a.bq, a.ent, a.bcnt, AN, b, false, true);
     warp_max_to<R>(rmax, red);
+  }
+  if (N > 0) {
+    typedef typename Vec2<R>::T V;
+    for (int b = rtid; b < nband; b += nth) {
+      const R j0x = a.bq[8 * b + 1], j0y = a.bq[8 * b + 2];
+      const Ent<R>* e = a.ent + (long long)b * kBandCap;
+      Ent<R> q[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) q[j] = e[j];
+      const int cnt = a.bcnt[b];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j >= cnt) { q[j].m = 0; q[j].w = R(0); }
+      R sxx = R(0), sxy = R(0), syy = R(0), dx = R(0), dy = R(0);
+      for (int n = 0; n <= N; ++n) {
+        const R* An = a.Ah + (long long)n * 2 * M;
+        const V* Av = reinterpret_cast<const V*>(An);
+        V v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = Av[q[j].m];
+        R px = R(0), py = R(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          px += q[j].w * v[j].x;
+          py += q[j].w * v[j].y;
+        }
+        if (cnt > 8) sparse_dot<R>(e + 8, cnt - 8, An, 0, px, py);
+        if (n < N) {
+          const R jx = j0x + px, jy = j0y + py;
+          sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
+        } else {
+          dx = px; dy = py;
+        }
+      }
+      a.bq[8 * b + 3] = sxx;
+      a.bq[8 * b + 4] = sxy;
+      a.bq[8 * b + 5] = syy;
+      a.bq[8 * b + 6] = dx;
+      a.bq[8 * b + 7] = dy;
+    }
   }
   grid_barrier<R>(a.bar, a.ctr, red, a.resid + N);
 
