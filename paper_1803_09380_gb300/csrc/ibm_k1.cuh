@@ -120,27 +120,35 @@ __device__ __forceinline__ void odd_node(const Geom& g, const StepConsts<typenam
 }
 
 // ------------------------------------------------------------------ vectors
-// VEC consecutive nodes per thread, moved as one 16-byte access per slot.
+// VEC consecutive nodes per thread, moved as one vector access per slot:
+// four nodes (16 bytes in FP32, 8 bytes in 16-bit storage) or two FP64
+// nodes (16 bytes).
 template <int P>
 struct VecTraits {
   typedef typename Prec<P>::S S;
-  static constexpr int VEC = 16 / (int)sizeof(S);
+  static constexpr int VEC = sizeof(S) == 8 ? 2 : 4;
 };
 
+template <int BYTES> struct VecWord;
+template <> struct VecWord<8> { typedef uint2 T; };
+template <> struct VecWord<16> { typedef uint4 T; };
+
 template <class S, int VEC>
-struct alignas(16) SVec {
+struct alignas(sizeof(S) * VEC) SVec {
   S v[VEC];
 };
 
 template <class S, int VEC>
 __device__ __forceinline__ SVec<S, VEC> vload(const S* p) {
+  typedef typename VecWord<sizeof(S) * VEC>::T T;
   SVec<S, VEC> r;
-  *reinterpret_cast<uint4*>(&r) = *reinterpret_cast<const uint4*>(p);
+  *reinterpret_cast<T*>(&r) = *reinterpret_cast<const T*>(p);
   return r;
 }
 template <class S, int VEC>
 __device__ __forceinline__ void vstore(S* p, const SVec<S, VEC>& r) {
-  *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(&r);
+  typedef typename VecWord<sizeof(S) * VEC>::T T;
+  *reinterpret_cast<T*>(p) = *reinterpret_cast<const T*>(&r);
 }
 
 template <class S>
@@ -203,7 +211,7 @@ __device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typenam
 // Odd step for one warp span of 32 * VEC consecutive nodes of row y that
 // holds no boundary node (every lane active; periodic wrap only across the
 // row ends).  Each lane owns nodes x0 .. x0+VEC-1.  Loads and stores are
-// aligned 16-byte vectors; the one-element shift of the directions with an
+// aligned vectors; the one-element shift of the directions with an
 // x component is done with warp shuffles.  Elements that cross to the
 // neighbouring span are read or written with scalar accesses by the thread
 // whose node owns the slot (lane 0 and lane 31), so spans never write each

@@ -5,8 +5,8 @@
 //
 // Collide+stream is HBM-bound: every node reads its nine populations once and
 // writes them once (18 s bytes per node update, s = bytes per stored
-// population).  Each thread owns 16 bytes of consecutive nodes of a row (4 in
-// FP32), so every access is an aligned 16-byte vector.  The even step touches
+// population).  Each thread owns 4 consecutive nodes of a row (2 in FP64), so
+// every access is one aligned 8- or 16-byte vector.  The even step touches
 // only the thread's own nodes.  The odd step reads each population from the
 // neighbour it streams from and writes it to the neighbour it streams to:
 // the one-element shift is done with warp shuffles (see odd_vec).  Nodes on
@@ -24,8 +24,8 @@
 namespace ibm {
 
 // One time step of collide+stream.  PAR 0: even step, 1: odd step.  A warp
-// covers one span of 32 * VEC consecutive nodes of a row (VEC = 16 bytes of
-// populations), each lane VEC nodes.
+// covers one span of 32 * VEC consecutive nodes of a row, each lane VEC
+// nodes.
 // MODE K1_ALL: every node.
 // MODE K1_MAIN: every node outside the 32-node segments that hold band nodes
 //   (the correction-loop kernel streams those segments after correcting
