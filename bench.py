@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-budget", type=float, default=20.0,
                    help="seconds of oracle work for the cpu_baseline sample")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=64)
+    p.add_argument("--serve-steps", type=int, default=500)
     return p.parse_args()
 
 
@@ -262,14 +265,56 @@ def run_ours(args, rank, world, local_rank, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args)
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(args, local_rank)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": DTYPE[args.prec], "data": "synthetic",
                 "config": workload_config(args, case), "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "serving": serving}
         print(json.dumps(line), flush=True)
+
+
+def run_serving(args, local_rank):
+    """Continuous batching on a bounded request stream shaped like the
+    serving workload (seeded Poisson arrivals; Couette N 64-512, fixed
+    cylinder lattices 200x100 to 800x400 with Re 10-100, one or two settling
+    disks of D 10-30), FP32, every request `serve_steps` time steps.  The
+    same requests are then run one at a time through the same API."""
+    from paper_1803_09380_gb300 import ibm
+    from paper_1803_09380_gb300 import workloads as wl
+    stream = wl.serving_stream(n_requests=args.serve_requests, seed=1803, rate_hz=2000.0,
+                               steps=args.serve_steps, couette_n=(64, 512), cyl_ny=(100, 400),
+                               box=(100, 300), disk_d=(10.0, 30.0))
+    out = {"requests": len(stream), "steps_per_request": args.serve_steps, "precision": "fp32",
+           "mix": "Couette N 64-512 log-uniform, cylinder 2ny x ny (ny 100-400, Re 10-100), "
+                  "1-2 settling disks D 10-30 in 100x300; Poisson arrivals at 2000/s, seed 1803"}
+    with ibm.Server(device=local_rank, max_active=32, steps_per_launch=100) as srv:
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(stream) or srv.stats()["completed"] + srv.stats()["failed"] < len(stream):
+            now = time.perf_counter() - t0
+            while k < len(stream) and stream[k][0] <= now:
+                srv.submit(stream[k][1], stream[k][2], prec="fp32", outputs=ibm.OUT_RESIDUAL)
+                k += 1
+            srv.progress()
+        st = srv.stats()
+    out.update({"solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"],
+                "p99_ms": st["p99_ms"], "mlups": st["mlups"], "failed": st["failed"],
+                "max_active": 32})
+    with ibm.Server(device=local_rank, max_active=1, steps_per_launch=100) as srv:
+        t0 = time.perf_counter()
+        for _, case, steps in stream:
+            cid = srv.submit(case, steps, prec="fp32", outputs=ibm.OUT_RESIDUAL)
+            srv.wait(cid)
+        dt = time.perf_counter() - t0
+    out["solves_per_s_one_at_a_time"] = len(stream) / dt
+    out["speedup_vs_one_at_a_time"] = out["solves_per_s"] / out["solves_per_s_one_at_a_time"]
+    return out
 
 
 def run_e2e(args, case, local_rank, dist, world):

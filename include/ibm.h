@@ -185,6 +185,19 @@ ibm_status ibm_get_sizes(ibm_handle h, long long *nodes, int *markers, int *bodi
  * Either pointer may be NULL. */
 ibm_status ibm_get_counters(ibm_handle h, long long *kernel_launches, long long *steps);
 
+/* Tuning options for ibm_set_option. */
+enum {
+  IBM_OPT_IB_CTAS = 1   /* CTAs of the correction kernel: 0 (default) = one CTA for up to 512
+                           markers, one per SM above that; n > 0 = min(n, SMs).  Results do not
+                           depend on it. */
+};
+
+/* Sets a tuning option of h (takes effect at the next step).  Concurrency
+ * note: the correction kernel of a lattice with more than one CTA holds all
+ * its CTAs resident while it runs; step at most two such lattices at once
+ * on one GPU (the server below enforces a budget). */
+ibm_status ibm_set_option(ibm_handle h, int option, long long value);
+
 /* Frees every device and host resource of h (NULL is a no-op). */
 ibm_status ibm_destroy(ibm_handle h);
 
@@ -198,6 +211,68 @@ const char *ibm_last_error(ibm_handle h);
 typedef void *(*ibm_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
 typedef void (*ibm_free_fn)(void *ptr, int device, void *stream, void *ctx);
 ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn release, void *ctx);
+
+/* ------------------------------------------------------------------ serving
+ * A server keeps many independent cases resident on one GPU and runs them
+ * concurrently (continuous batching; the paper has no counterpart, this is
+ * the deployment layer around ibm_step).  Submitted cases wait in a FIFO
+ * and are admitted while the device-memory budget, the slot count and the
+ * correction-kernel CTA budget allow; each admitted case gets its own
+ * lattice and stream and is advanced in chunks of steps (CUDA-graph
+ * replays), so kernels of different cases overlap on the device.  When a
+ * case has taken its steps, its requested outputs are copied to host
+ * memory, its device memory is released and the next waiting case is
+ * admitted.  A case's results do not depend on what else runs with it. */
+typedef struct ibm_server_s *ibm_server;
+
+typedef struct {
+  int device;
+  double max_device_bytes;    /* budget for resident cases; <= 0: 80% of free memory */
+  int max_active;             /* resident cases at once (slots), >= 1 */
+  int steps_per_launch;       /* steps enqueued per case per round, >= 1 */
+  int ib_cta_budget;          /* sum of correction-kernel CTAs of resident cases; <= 0: 2 per SM */
+} ibm_server_desc;
+
+enum { IBM_OUT_MACRO = 1, IBM_OUT_BODIES = 2, IBM_OUT_RESIDUAL = 4 };
+
+typedef struct {
+  ibm_lattice_desc lattice;   /* cuda_stream and device are set by the server */
+  int nbodies;
+  const ibm_body_desc *bodies;
+  const int *nmarkers;        /* markers per body */
+  const double *xy;           /* all markers, interleaved, body after body */
+  const double *ds;           /* arc lengths of all markers, or NULL */
+  int nsteps;                 /* time steps of the case */
+  unsigned outputs;           /* IBM_OUT_* */
+} ibm_case_desc;
+
+typedef struct {
+  long long submitted, completed, active, pending, failed;
+  double p50_ms, p95_ms, p99_ms, mean_ms;  /* time to solution: submission to results in host memory */
+  double solves_per_s;        /* completed / (last completion - first submission) */
+  double mlups;               /* lattice updates of completed cases over the same interval */
+  double device_bytes;        /* estimated device memory of resident cases */
+} ibm_server_stats;
+
+ibm_status ibm_server_create(const ibm_server_desc *desc, ibm_server *out);
+/* Copies the case; *case_id receives its id.  Never blocks on the GPU. */
+ibm_status ibm_server_submit(ibm_server s, const ibm_case_desc *c, long long *case_id);
+/* Harvests finished chunks, launches next chunks, admits waiting cases;
+ * *completed (optional) receives the number of cases finished by this call.
+ * Never blocks on the GPU. */
+ibm_status ibm_server_progress(ibm_server s, int *completed);
+/* Runs progress until the case (case_id >= 0) or every case (case_id < 0)
+ * is finished. */
+ibm_status ibm_server_wait(ibm_server s, long long case_id);
+/* Outputs of a finished case: IBM_FIELD_RHO / UX / UY ([ny][nx]),
+ * IBM_FIELD_BODIES ([nbodies][9]) or IBM_FIELD_RESIDUAL ([n_corr + 1]) of its
+ * last step, if requested at submission.  Returns the case's own failure
+ * status if it failed. */
+ibm_status ibm_server_result(ibm_server s, long long case_id, int field, double *host_dst, size_t n_elems);
+ibm_status ibm_server_release(ibm_server s, long long case_id);   /* drops stored results */
+ibm_status ibm_server_get_stats(ibm_server s, ibm_server_stats *out);
+ibm_status ibm_server_destroy(ibm_server s);
+const char *ibm_server_last_error(ibm_server s);
 
 /* The correction loop of one step for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment variant of the

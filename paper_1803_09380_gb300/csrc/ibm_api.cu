@@ -11,7 +11,6 @@
 
 using namespace ibm;
 
-struct ibm_ctx : public Ctx {};
 
 namespace {
 
@@ -187,7 +186,12 @@ ibm_status upload_markers(Ctx* h) {
   IBM_ALLOC(h, c.dbnode, int*, c.bcap);
   IBM_ALLOC(h, c.dbcnt, int*, c.bcap);
   c.dent = dev_alloc(c, (R == 8 ? sizeof(Ent<double>) : sizeof(Ent<float>)) * (size_t)c.bcap * kBandCap);
-  IBM_ALLOC(h, c.dfpart, double*, (size_t)c.ib_grid * c.nb * 3);
+  IBM_ALLOC(h, c.dfpart, double*, (size_t)((M + kForceChunk - 1) / kForceChunk) * c.nb * 3);
+  // correction-kernel CTAs: one for small boundaries (its grid barrier is a
+  // block barrier, so such kernels of several lattices may run side by
+  // side), one per SM otherwise
+  c.ib_grid = c.ib_grid_opt > 0 ? (c.ib_grid_opt < c.ib_grid_max ? c.ib_grid_opt : c.ib_grid_max)
+                                : (M <= kSmallIbMarkers ? 1 : c.ib_grid_max);
   c.dbq = dev_alloc(c, R * 8 * (size_t)c.bcap);
   c.dmq = dev_alloc(c, R * 4 * (size_t)M);
   c.dAh = dev_alloc(c, R * 2 * (size_t)M * (c.desc.n_corr + 1));
@@ -352,6 +356,7 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
       return bail(IBM_ERR_CUDA);
     }
     c.ib_grid = sms;
+    c.ib_grid_max = sms;
     if (cudaStreamCreateWithPriority(&c.ib_stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -693,6 +698,22 @@ ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodi
     IBM_CK(h, cudaStreamSynchronize(h->stream));
     if (band_nodes) *band_nodes = h->nm > 0 ? ctr[CTR_NBAND] : 0;
     if (band_segments) *band_segments = h->nm > 0 ? ctr[CTR_NSEG] : 0;
+  }
+  return IBM_OK;
+}
+
+ibm_status ibm_set_option(ibm_handle h, int option, long long value) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (option != IBM_OPT_IB_CTAS) return fail(h, IBM_ERR_INVALID, "unknown option");
+  if (value < 0 || value > (1 << 20)) return fail(h, IBM_ERR_INVALID, "IBM_OPT_IB_CTAS out of range");
+  h->ib_grid_opt = (int)value;
+  const int M = h->nm;
+  h->ib_grid = h->ib_grid_opt > 0 ? (h->ib_grid_opt < h->ib_grid_max ? h->ib_grid_opt : h->ib_grid_max)
+                                  : (M <= kSmallIbMarkers ? 1 : h->ib_grid_max);
+  {
+    DeviceGuard guard(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(*h);
   }
   return IBM_OK;
 }

@@ -254,7 +254,7 @@ struct IbArgs {
   const double* X;
   const double* Y;
   const double* ds;
-  double* fpart;              // [gridDim][nb][3]
+  double* fpart;              // [chunks][nb][3]
   unsigned long long* bar;    // grid-barrier arrivals (monotonic)
 };
 
@@ -268,12 +268,16 @@ template <class R>
 __device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr, const R* red = nullptr,
                                              R* dst = nullptr) {
   __syncthreads();
+  if (threadIdx.x == 0 && dst) {
+    R m = red[0];
+    for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
+    if (m > R(0) || m != m) AtomicBits<R>::max(dst, m);
+  }
+  if (gridDim.x == 1) {                           // one CTA: a block barrier suffices
+    __syncthreads();
+    return;
+  }
   if (threadIdx.x == 0) {
-    if (dst) {
-      R m = red[0];
-      for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
-      if (m > R(0) || m != m) AtomicBits<R>::max(dst, m);
-    }
     __threadfence();
     const unsigned long long g = gridDim.x;
     const unsigned long long t = atomicAdd(bar, 1ull) + 1ull;
@@ -581,26 +585,30 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
     }
   }
 
-  // Eq. 29: per-CTA partial force and torque of each body over a fixed
-  // chunk of markers, F_l = -ds_l A^N_l, T_l = (X_l - x_c) x F_l (FP64).
-  const int chunk = (M + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * chunk, hi = min(M, lo + chunk);
-  if (a.nb > 0 && lo < hi) {
-    const int b0 = a.mbody[lo], b1 = a.mbody[hi - 1];
-    for (int bd = b0; bd <= b1; ++bd) {
-      const BodyDev& B = a.bodies[bd];
-      const int l0 = max(lo, B.m0), l1 = min(hi, B.m1);
-      double fx = 0.0, fy = 0.0, tq = 0.0;
-      for (int l = l0 + (int)threadIdx.x; l < l1; l += blockDim.x) {
-        const double Fx = -a.ds[l] * (double)AN[2 * l], Fy = -a.ds[l] * (double)AN[2 * l + 1];
-        fx += Fx;
-        fy += Fy;
-        tq += (a.X[l] - B.xc[0]) * Fy - (a.Y[l] - B.xc[1]) * Fx;
-      }
-      block_sum3(fx, fy, tq, sh);
-      if (threadIdx.x == 0) {
-        double* o = a.fpart + ((long long)blockIdx.x * a.nb + bd) * 3;
-        o[0] = fx; o[1] = fy; o[2] = tq;
+  // Eq. 29: partial force and torque of each body over fixed chunks of
+  // kForceChunk markers (CTAs take chunks in turn), F_l = -ds_l A^N_l,
+  // T_l = (X_l - x_c) x F_l, FP64; the chunking does not depend on the grid,
+  // so neither do the sums.
+  const int nchunk = (M + kForceChunk - 1) / kForceChunk;
+  if (a.nb > 0) {
+    for (int k = blockIdx.x; k < nchunk; k += gridDim.x) {
+      const int lo = k * kForceChunk, hi = min(M, lo + kForceChunk);
+      const int b0 = a.mbody[lo], b1 = a.mbody[hi - 1];
+      for (int bd = b0; bd <= b1; ++bd) {
+        const BodyDev& B = a.bodies[bd];
+        const int l0 = max(lo, B.m0), l1 = min(hi, B.m1);
+        double fx = 0.0, fy = 0.0, tq = 0.0;
+        for (int l = l0 + (int)threadIdx.x; l < l1; l += blockDim.x) {
+          const double Fx = -a.ds[l] * (double)AN[2 * l], Fy = -a.ds[l] * (double)AN[2 * l + 1];
+          fx += Fx;
+          fy += Fy;
+          tq += (a.X[l] - B.xc[0]) * Fy - (a.Y[l] - B.xc[1]) * Fx;
+        }
+        block_sum3(fx, fy, tq, sh);
+        if (threadIdx.x == 0) {
+          double* o = a.fpart + ((long long)k * a.nb + bd) * 3;
+          o[0] = fx; o[1] = fy; o[2] = tq;
+        }
       }
     }
   }
@@ -609,7 +617,7 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
   // body totals: one body per CTA, fixed-shape reduction over the chunks
   for (int bd = blockIdx.x; bd < a.nb; bd += gridDim.x) {
     BodyDev& B = a.bodies[bd];
-    const int k0 = B.m0 / chunk, k1 = (B.m1 - 1) / chunk;
+    const int k0 = B.m0 / kForceChunk, k1 = (B.m1 - 1) / kForceChunk;
     double f0 = 0.0, f1 = 0.0, f2 = 0.0;
     for (int k = k0 + (int)threadIdx.x; k <= k1; k += blockDim.x) {
       const double* o = a.fpart + ((long long)k * a.nb + bd) * 3;
@@ -798,7 +806,7 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   // the band segments, once corrected
   if (h.band_collide) {
     const int need = (h.segcap * kSegW + 255) / 256;
-    const dim3 g2(need < 8 * h.ib_grid ? (need > 0 ? need : 1) : 8 * h.ib_grid), b2(256);
+    const dim3 g2(need < 8 * h.ib_grid_max ? (need > 0 ? need : 1) : 8 * h.ib_grid_max), b2(256);
     const int* ctr = a.ctr;
     if (parity == 0) {
       if (macro) launch_prio(k_band_collide<P, 0, true>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);

@@ -34,6 +34,8 @@ struct alignas(2 * sizeof(R) > 8 ? 16 : 8) Ent {
 
 constexpr int kIbThreads = 256;                  // threads per correction-loop CTA
 constexpr int kGCap = 64;                        // coupled markers per marker (G row)
+constexpr int kForceChunk = 128;                 // markers per partial force sum
+constexpr int kSmallIbMarkers = 512;             // up to this many markers: one correction CTA
 constexpr long long kBarrierCycles = 4000000000LL; // ~2 s at 2 GHz: grid-barrier wait limit
 
 // Device counters: band nodes, band row segments, error bits.
@@ -103,9 +105,11 @@ struct Ctx {
   int* dsegflag = nullptr;                   // [ny][nseg_x] 1 if the segment has a band node
   int* dseglist = nullptr;                   // [segcap] band segments
   BodyDev* dbodies = nullptr;
-  double* dfpart = nullptr;                  // [ib_grid][nb][3] force partial sums
+  double* dfpart = nullptr;                  // [chunks][nb][3] force partial sums
   unsigned long long* dbar = nullptr;        // grid-barrier arrivals of the correction kernel
-  int ib_grid = 0;                           // CTAs of the correction kernel (one per SM)
+  int ib_grid = 0;                           // CTAs of the correction kernel
+  int ib_grid_max = 0;                       // one per SM
+  int ib_grid_opt = 0;                       // caller's choice (IBM_OPT_IB_CTAS), 0 = by size
   bool band_collide = true;                  // stream the band segments after the correction
   bool band_valid = false;
 
@@ -129,6 +133,13 @@ struct Ctx {
   std::vector<void*> allocs;
   std::string err;
 };
+
+}  // namespace ibm
+
+// The object behind an ibm_handle.
+struct ibm_ctx : public ibm::Ctx {};
+
+namespace ibm {
 
 // Number of CUDA kernels one time step launches (matches enqueue_step).
 inline int kernels_per_step(const Ctx& h) {

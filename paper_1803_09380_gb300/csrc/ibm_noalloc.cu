@@ -168,6 +168,7 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
   c.nseg_x = (nx + kSegW - 1) / kSegW;
   c.segcap = c.bcap;
   c.ib_grid = sms;
+  c.ib_grid_max = sms;
   c.ib_prio = 0;
   c.band_collide = false;                   // correction only
   const size_t R = c.r_bytes;
@@ -202,7 +203,7 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
   c.dgcnt = cv.take<int>(n_markers);
   c.dresid = cv.take<unsigned char>(R * (n_corr + 1));
   c.dbodies = cv.take<BodyDev>(1);
-  c.dfpart = cv.take<double>((size_t)sms * 3);
+  c.dfpart = cv.take<double>((size_t)((n_markers + kForceChunk - 1) / kForceChunk) * 3);
   if (!c.dfpart)
     return na_fail(IBM_ERR_INVALID, "ibm_ib_correct_noalloc: the scratch array is too small for this call");
 

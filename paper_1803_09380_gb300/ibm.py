@@ -34,7 +34,12 @@ _STATUS = {0: "IBM_OK", 1: "IBM_ERR_INVALID", 2: "IBM_ERR_NOMEM", 3: "IBM_ERR_CU
 SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields",
            "ibm_write_fields", "ibm_sync", "ibm_kernel_times", "ibm_get_sizes",
            "ibm_get_counters", "ibm_destroy", "ibm_last_error", "ibm_set_allocator",
-           "ibm_abi_version", "ibm_ib_correct_noalloc")
+           "ibm_abi_version", "ibm_ib_correct_noalloc", "ibm_set_option",
+           "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_wait",
+           "ibm_server_result", "ibm_server_release", "ibm_server_get_stats", "ibm_server_destroy",
+           "ibm_server_last_error")
+IBM_OPT_IB_CTAS = 1
+OUT_MACRO, OUT_BODIES, OUT_RESIDUAL = 1, 2, 4
 
 
 class IBMError(RuntimeError):
@@ -58,6 +63,28 @@ class BodyDesc(ctypes.Structure):
                 ("rho_s", ctypes.c_double), ("rho_f", ctypes.c_double),
                 ("volume", ctypes.c_double), ("inertia", ctypes.c_double),
                 ("radius", ctypes.c_double), ("gravity", ctypes.c_double * 2)]
+
+
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_device_bytes", ctypes.c_double),
+                ("max_active", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
+                ("ib_cta_budget", ctypes.c_int)]
+
+
+class CaseDesc(ctypes.Structure):
+    _fields_ = [("lattice", LatticeDesc), ("nbodies", ctypes.c_int),
+                ("bodies", ctypes.POINTER(BodyDesc)), ("nmarkers", ctypes.POINTER(ctypes.c_int)),
+                ("xy", ctypes.POINTER(ctypes.c_double)), ("ds", ctypes.POINTER(ctypes.c_double)),
+                ("nsteps", ctypes.c_int), ("outputs", ctypes.c_uint)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("active", ctypes.c_longlong), ("pending", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("p95_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double),
+                ("mlups", ctypes.c_double), ("device_bytes", ctypes.c_double)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
@@ -105,8 +132,19 @@ def load(build_if_missing: bool = True):
         lib.ibm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
         lib.ibm_abi_version.restype = ci
         lib.ibm_ib_correct_noalloc.argtypes = [ci, ci, ci, vp, ci, vp, vp, vp, ci, vp, vp, vp]
+        lib.ibm_set_option.argtypes = [vp, ci, ctypes.c_longlong]
+        lib.ibm_server_create.argtypes = [ctypes.POINTER(ServerDesc), ctypes.POINTER(vp)]
+        lib.ibm_server_submit.argtypes = [vp, ctypes.POINTER(CaseDesc), ctypes.POINTER(ctypes.c_longlong)]
+        lib.ibm_server_progress.argtypes = [vp, ctypes.POINTER(ci)]
+        lib.ibm_server_wait.argtypes = [vp, ctypes.c_longlong]
+        lib.ibm_server_result.argtypes = [vp, ctypes.c_longlong, ci, _D, ctypes.c_size_t]
+        lib.ibm_server_release.argtypes = [vp, ctypes.c_longlong]
+        lib.ibm_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.ibm_server_destroy.argtypes = [vp]
+        lib.ibm_server_last_error.argtypes = [vp]
+        lib.ibm_server_last_error.restype = ctypes.c_char_p
         for name in SYMBOLS:
-            if name not in ("ibm_last_error", "ibm_abi_version"):
+            if name not in ("ibm_last_error", "ibm_abi_version", "ibm_server_last_error"):
                 getattr(lib, name).restype = ci
         _lib = lib
         return lib
@@ -284,6 +322,159 @@ def ibm_ib_correct_noalloc(nx, ny, prec, f_ptr, n_markers, xy_ptr, ds_ptr, uvel_
     _check(load().ibm_ib_correct_noalloc(int(nx), int(ny), p, f_ptr, int(n_markers), xy_ptr, ds_ptr,
                                          uvel_ptr, int(n_corr), resid_ptr, force_ptr, stream),
            None, "ibm_ib_correct_noalloc")
+
+
+def ibm_set_option(h, option: int, value: int) -> None:
+    _check(load().ibm_set_option(h, int(option), int(value)), h, "ibm_set_option")
+
+
+def _scheck(st: int, srv, where: str) -> int:
+    if st == IBM_OK:
+        return st
+    msg = load().ibm_server_last_error(srv).decode(errors="replace")
+    raise IBMError(st, where, msg)
+
+
+def ibm_server_create(device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=100,
+                      ib_cta_budget=0):
+    d = ServerDesc(int(device), float(max_device_bytes), int(max_active), int(steps_per_launch),
+                   int(ib_cta_budget))
+    srv = ctypes.c_void_p()
+    _scheck(load().ibm_server_create(ctypes.byref(d), ctypes.byref(srv)), None, "ibm_server_create")
+    return srv
+
+
+def _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol=0.0):
+    d = LatticeDesc()
+    d.nx, d.ny, d.tau, d.rho0 = int(nx), int(ny), float(tau), float(rho0)
+    d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    for k in range(4):
+        d.bc[k] = int(bc[k])
+    wu = np.zeros(8) if wall_u is None else np.asarray(wall_u, dtype=np.float64).reshape(8)
+    for k in range(4):
+        d.wall_u[k][0], d.wall_u[k][1] = float(wu[2 * k]), float(wu[2 * k + 1])
+    d.inlet_u[0], d.inlet_u[1] = float(inlet_u[0]), float(inlet_u[1])
+    d.n_corr, d.corr_tol, d.delta_points = int(n_corr), float(corr_tol), 4
+    return d
+
+
+def _body_desc(b) -> BodyDesc:
+    bd = BodyDesc()
+    bd.kind = int(b.kind)
+    bd.xc[0], bd.xc[1] = float(b.xc[0]), float(b.xc[1])
+    bd.u[0], bd.u[1] = float(b.u[0]), float(b.u[1])
+    bd.omega, bd.theta = float(b.omega), float(b.theta)
+    bd.rho_s, bd.rho_f, bd.volume = float(b.rho_s), float(b.rho_f), float(b.volume)
+    bd.inertia, bd.radius = float(b.inertia), float(b.radius)
+    bd.gravity[0], bd.gravity[1] = float(b.gravity[0]), float(b.gravity[1])
+    return bd
+
+
+def ibm_server_submit(srv, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BODIES | OUT_RESIDUAL) -> int:
+    """Submit a workloads.Case for nsteps time steps; returns its id."""
+    c = CaseDesc()
+    c.lattice = _lattice_desc(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u,
+                              case.inlet_u, case.n_corr)
+    nb = len(case.bodies)
+    bodies = (BodyDesc * max(nb, 1))(*[_body_desc(b) for b in case.bodies])
+    nmark = (ctypes.c_int * max(nb, 1))(*[b.xy.shape[0] for b in case.bodies])
+    xy = np.ascontiguousarray(np.concatenate([b.xy for b in case.bodies]) if nb else np.zeros((0, 2)))
+    ds = np.ascontiguousarray(np.concatenate([b.ds for b in case.bodies]) if nb else np.zeros(0))
+    c.nbodies = nb
+    c.bodies = bodies
+    c.nmarkers = nmark
+    c.xy = xy.ctypes.data_as(_D)
+    c.ds = ds.ctypes.data_as(_D)
+    c.nsteps = int(nsteps)
+    c.outputs = int(outputs)
+    cid = ctypes.c_longlong()
+    _scheck(load().ibm_server_submit(srv, ctypes.byref(c), ctypes.byref(cid)), srv, "ibm_server_submit")
+    return cid.value
+
+
+def ibm_server_progress(srv) -> int:
+    n = ctypes.c_int()
+    _scheck(load().ibm_server_progress(srv, ctypes.byref(n)), srv, "ibm_server_progress")
+    return n.value
+
+
+def ibm_server_wait(srv, case_id=-1) -> None:
+    _scheck(load().ibm_server_wait(srv, int(case_id)), srv, "ibm_server_wait")
+
+
+def ibm_server_result(srv, case_id, field, shape):
+    out = np.empty(shape, dtype=np.float64)
+    _scheck(load().ibm_server_result(srv, int(case_id), int(field), out.ctypes.data_as(_D), out.size),
+            srv, "ibm_server_result")
+    return out
+
+
+def ibm_server_release(srv, case_id) -> None:
+    _scheck(load().ibm_server_release(srv, int(case_id)), srv, "ibm_server_release")
+
+
+def ibm_server_get_stats(srv) -> dict:
+    st = ServerStats()
+    _scheck(load().ibm_server_get_stats(srv, ctypes.byref(st)), srv, "ibm_server_get_stats")
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def ibm_server_destroy(srv) -> None:
+    if srv is not None and srv.value:
+        load().ibm_server_destroy(srv)
+        srv.value = None
+
+
+def ibm_server_last_error(srv=None) -> str:
+    return load().ibm_server_last_error(srv).decode(errors="replace")
+
+
+class Server:
+    """Owning wrapper of an ibm_server (context manager)."""
+
+    def __init__(self, device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=100,
+                 ib_cta_budget=0):
+        self.s = ibm_server_create(device, max_device_bytes, max_active, steps_per_launch, ib_cta_budget)
+        self._shapes = {}
+
+    def submit(self, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BODIES | OUT_RESIDUAL) -> int:
+        cid = ibm_server_submit(self.s, case, nsteps, prec, outputs)
+        self._shapes[cid] = (case.ny, case.nx, len(case.bodies), case.n_corr)
+        return cid
+
+    def progress(self) -> int:
+        return ibm_server_progress(self.s)
+
+    def wait(self, case_id=-1):
+        ibm_server_wait(self.s, case_id)
+
+    def result(self, case_id, field):
+        ny, nx, nb, nc = self._shapes[case_id]
+        shape = {FIELD_RHO: (ny, nx), FIELD_UX: (ny, nx), FIELD_UY: (ny, nx),
+                 FIELD_BODIES: (nb, 9), FIELD_RESIDUAL: (nc + 1,)}[field]
+        return ibm_server_result(self.s, case_id, field, shape)
+
+    def release(self, case_id):
+        ibm_server_release(self.s, case_id)
+
+    def stats(self) -> dict:
+        return ibm_server_get_stats(self.s)
+
+    def close(self):
+        if getattr(self, "s", None) is not None and self.s.value:
+            ibm_server_destroy(self.s)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ibm_last_error(h=None) -> str:

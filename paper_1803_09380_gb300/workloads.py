@@ -194,3 +194,39 @@ def random_perturbation(nx: int, ny: int, seed: int, amplitude: float = 1e-3):
     """Seeded random array of shape (9, ny, nx) to add to populations."""
     rng = np.random.default_rng(seed)
     return amplitude * rng.standard_normal((9, ny, nx))
+
+
+def serving_stream(n_requests: int = 512, seed: int = 1803, rate_hz: float = 200.0,
+                   steps: int = 1000, couette_n=(64, 2048), cyl_ny=(200, 800),
+                   cyl_re=(10.0, 100.0), box=(200, 600), disk_d=(10.0, 30.0)):
+    """A seeded request stream: Poisson arrivals at rate_hz, families drawn
+    uniformly from {Couette with N log-uniform in couette_n, fixed cylinder
+    with Re uniform in cyl_re on lattices 2 ny x ny (ny in cyl_ny, D = ny/20),
+    one or two settling disks with D uniform in disk_d in a box}; every
+    request runs `steps` time steps.  Returns [(arrival_s, Case, steps)]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n_requests):
+        t += rng.exponential(1.0 / rate_hz)
+        fam = int(rng.integers(0, 3))
+        if fam == 0:
+            n = int(round(math.exp(rng.uniform(math.log(couette_n[0]), math.log(couette_n[1])))))
+            n = max(32, n)
+            case = couette(n)
+        elif fam == 1:
+            ny = int(rng.integers(cyl_ny[0] // 10, cyl_ny[1] // 10 + 1)) * 10
+            d = ny / 20.0
+            case = cylinder(nx=2 * ny, ny=ny, diameter=d, center=(ny / 2.0, ny / 2.0 + 0.3),
+                            u_in=0.05, re=float(rng.uniform(*cyl_re)),
+                            markers=max(16, int(round(math.pi * d))))
+        else:
+            nx, ny = box
+            d = float(rng.uniform(*disk_d))
+            bodies = [disk(nx / 2.0 + 0.1 * d, ny - 3.0 * d, d, 1.2, 1e-4)]
+            if rng.random() < 0.5:
+                bodies.append(disk(nx / 2.0, ny - 5.5 * d, d, 1.2, 1e-4))
+            case = Case(f"settle_{len(bodies)}", nx, ny, 0.8, bc=(BOUNCEBACK,) * 4, bodies=bodies,
+                        meta=dict(diameter=d))
+        out.append((t, case, steps))
+    return out
