@@ -20,6 +20,10 @@ from __future__ import annotations
 import argparse
 import json
 import os
+
+# 32 hardware work queues instead of CUDA's default 8, before any CUDA
+# context exists: the serving section keeps dozens of cases' streams busy.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import statistics
 import subprocess
 import sys
@@ -38,7 +42,7 @@ def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=2000)
-    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=500)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--prec", choices=list(BYTES_PER_POP), default="fp32")
@@ -50,6 +54,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-requests", type=int, default=64)
     p.add_argument("--serve-steps", type=int, default=500)
+    p.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
+    p.add_argument("--serve-active", type=int, default=32, help="cases resident at once")
     return p.parse_args()
 
 
@@ -280,39 +286,44 @@ def run_ours(args, rank, world, local_rank, dist):
 
 
 def run_serving(args, local_rank):
-    """Continuous batching on a bounded request stream shaped like the
-    serving workload (seeded Poisson arrivals; Couette N 64-512, fixed
-    cylinder lattices 200x100 to 800x400 with Re 10-100, one or two settling
-    disks of D 10-30), FP32, every request `serve_steps` time steps.  The
-    same requests are then run one at a time through the same API."""
+    """Continuous batching on a bounded request stream with the serving mix
+    (seeded Poisson arrivals; a uniform mix of Couette with N log-uniform in
+    64-2048, fixed cylinders on 2ny x ny lattices with ny in 200-800 and Re
+    10-100, and one or two settling disks of D 10-30 in a 200 x 600 box),
+    FP32, `serve_steps` time steps per request, arrivals fast enough to keep
+    the server saturated.  The same requests then run one at a time through
+    the same API (max_active = 1)."""
     from paper_1803_09380_gb300 import ibm
     from paper_1803_09380_gb300 import workloads as wl
-    stream = wl.serving_stream(n_requests=args.serve_requests, seed=1803, rate_hz=2000.0,
-                               steps=args.serve_steps, couette_n=(64, 512), cyl_ny=(100, 400),
-                               box=(100, 300), disk_d=(10.0, 30.0))
+    stream = wl.serving_stream(n_requests=args.serve_requests, seed=1803, rate_hz=args.serve_rate,
+                               steps=args.serve_steps)
     out = {"requests": len(stream), "steps_per_request": args.serve_steps, "precision": "fp32",
-           "mix": "Couette N 64-512 log-uniform, cylinder 2ny x ny (ny 100-400, Re 10-100), "
-                  "1-2 settling disks D 10-30 in 100x300; Poisson arrivals at 2000/s, seed 1803"}
-    with ibm.Server(device=local_rank, max_active=32, steps_per_launch=100) as srv:
-        t0 = time.perf_counter()
-        k = 0
-        while k < len(stream) or srv.stats()["completed"] + srv.stats()["failed"] < len(stream):
-            now = time.perf_counter() - t0
-            while k < len(stream) and stream[k][0] <= now:
+           "mix": "Couette N 64-2048 log-uniform, cylinder 2ny x ny (ny 200-800, Re 10-100), "
+                  f"1-2 settling disks D 10-30 in 200x600; Poisson arrivals at {args.serve_rate:g}/s, "
+                  "seed 1803"}
+
+    def serve(max_active, paced):
+        with ibm.Server(device=local_rank, max_active=max_active, steps_per_launch=32) as srv:
+            t0 = time.perf_counter()
+            k = 0
+            while k < len(stream):
+                if paced:
+                    while k < len(stream) and stream[k][0] > time.perf_counter() - t0:
+                        srv.progress()
                 srv.submit(stream[k][1], stream[k][2], prec="fp32", outputs=ibm.OUT_RESIDUAL)
                 k += 1
-            srv.progress()
-        st = srv.stats()
+                if not paced:
+                    srv.wait()
+            srv.wait()
+            wall = time.perf_counter() - t0
+            return srv.stats(), wall
+
+    st, wall = serve(args.serve_active, True)
     out.update({"solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"],
                 "p99_ms": st["p99_ms"], "mlups": st["mlups"], "failed": st["failed"],
-                "max_active": 32})
-    with ibm.Server(device=local_rank, max_active=1, steps_per_launch=100) as srv:
-        t0 = time.perf_counter()
-        for _, case, steps in stream:
-            cid = srv.submit(case, steps, prec="fp32", outputs=ibm.OUT_RESIDUAL)
-            srv.wait(cid)
-        dt = time.perf_counter() - t0
-    out["solves_per_s_one_at_a_time"] = len(stream) / dt
+                "max_active": args.serve_active, "wall_s": wall})
+    st1, wall1 = serve(1, False)
+    out["solves_per_s_one_at_a_time"] = len(stream) / wall1
     out["speedup_vs_one_at_a_time"] = out["solves_per_s"] / out["solves_per_s_one_at_a_time"]
     return out
 

@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define IBM_ABI_VERSION 1
+#define IBM_ABI_VERSION 2
 
 typedef struct ibm_ctx *ibm_handle; /* opaque, library-owned */
 
@@ -73,6 +73,11 @@ typedef enum {
   IBM_BC_OUTLET_ZEROGRAD = 4
 } ibm_bc;
 
+/* Collision operator.  BGK: Omega_i = -(f_i - f_i^eq)/tau.  MRT: Eq. 2
+ * with the transform matrix of Eq. 5 and the diagonal relaxation matrix of
+ * Eq. 6; with every rate equal to 1/tau it is BGK. */
+typedef enum { IBM_COLL_BGK = 0, IBM_COLL_MRT = 1 } ibm_collision;
+
 enum { IBM_SIDE_XMIN = 0, IBM_SIDE_XMAX = 1, IBM_SIDE_YMIN = 2, IBM_SIDE_YMAX = 3 };
 
 typedef struct {
@@ -91,6 +96,13 @@ typedef struct {
                                  creates its own stream, which synchronises
                                  with the legacy default stream */
   int device;                 /* CUDA device ordinal */
+  int collision;              /* ibm_collision; 0 (zero-initialised) is BGK */
+  double mrt_s[3];            /* MRT rates s_e, s_eps, s_q of Eq. 6 for the
+                                 energy, energy-square and energy-flux
+                                 moments, each in (0, 2); 0 takes the
+                                 values of section 3 (1.1, 1.25, 1.8).  The
+                                 stress moments relax at 1/tau (Eq. 8);
+                                 ignored for BGK */
 } ibm_lattice_desc;
 
 typedef enum { IBM_BODY_FIXED = 0, IBM_BODY_PRESCRIBED = 1, IBM_BODY_FREE = 2 } ibm_body_kind;
@@ -231,6 +243,9 @@ typedef struct {
   int max_active;             /* resident cases at once (slots), >= 1 */
   int steps_per_launch;       /* steps enqueued per case per round, >= 1 */
   int ib_cta_budget;          /* sum of correction-kernel CTAs of resident cases; <= 0: 2 per SM */
+  int ib_markers_per_cta;     /* a case with M markers runs its correction loop on
+                                 ceil(M / this) CTAs (one CTA when M <= this, at
+                                 most one per SM); <= 0: 512 */
 } ibm_server_desc;
 
 enum { IBM_OUT_MACRO = 1, IBM_OUT_BODIES = 2, IBM_OUT_RESIDUAL = 4 };
@@ -252,6 +267,9 @@ typedef struct {
   double solves_per_s;        /* completed / (last completion - first submission) */
   double mlups;               /* lattice updates of completed cases over the same interval */
   double device_bytes;        /* estimated device memory of resident cases */
+  double host_admit_s;        /* host seconds spent admitting cases (lattice set-up) */
+  double host_launch_s;       /* host seconds spent enqueuing chunks */
+  double host_harvest_s;      /* host seconds spent copying results out */
 } ibm_server_stats;
 
 ibm_status ibm_server_create(const ibm_server_desc *desc, ibm_server *out);

@@ -17,7 +17,11 @@ Parity status of the functions (what pins each one is in ``tests/``):
   walls (bounce-back, free-slip)  pinned by plane Poiseuille / plug flow
   inlet / outlet                  pinned by uniform-flow preservation
   whole step                      pinned by the analytic Couette profile
-                                  (Eq. 34) and its second-order slope
+                                  (Eq. 34) and its measured convergence slope
+  MRT collision (Eqs. 2, 5, 6)    pinned by the closed-form equilibrium
+                                  moments, reduction to BGK at equal rates,
+                                  per-moment relaxation factors 1 - s_k and
+                                  the shear-wave decay set by 1/tau alone
   Newton-Euler body update        parity unpinned beyond closed-form free
                                   fall with no fluid force (Eqs. 40-42)
 """
@@ -89,6 +93,9 @@ def _load():
         lib.ora_num_markers.argtypes = [vp]
         lib.ora_num_bodies.restype = ctypes.c_int
         lib.ora_num_bodies.argtypes = [vp]
+        lib.ora_set_mrt.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.ora_mrt_matrix.argtypes = [_D]
+        lib.ora_mrt_collide.argtypes = [_D, _D, _D, _D]
         _lib = lib
         return lib
 
@@ -117,8 +124,28 @@ def moments(p) -> tuple[float, float, float]:
     return r.value, jx.value, jy.value
 
 
+def mrt_matrix() -> np.ndarray:
+    """The transform matrix M of Eq. 5 as the oracle holds it."""
+    out = np.empty((9, 9))
+    _load().ora_mrt_matrix(_dp(out))
+    return out
+
+
+def mrt_collide(rates, p, fe) -> np.ndarray:
+    """One MRT collision (Eq. 2) at one node: p - M^-1 S M (p - fe) with
+    S = diag(rates) (Eq. 6, nine rates in the row order of Eq. 5)."""
+    s = np.ascontiguousarray(rates, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    fe = np.ascontiguousarray(fe, dtype=np.float64)
+    out = np.empty(9)
+    _load().ora_mrt_collide(_dp(s), _dp(p), _dp(fe), _dp(out))
+    return out
+
+
 class Lattice:
     """One oracle lattice: D2Q9 BGK with immersed bodies, all FP64.
+    ``mrt=(s_e, s_eps, s_q)`` switches the collision to MRT (Eqs. 2, 5, 6)
+    with the stress moments relaxing at 1/tau.
 
     ``bc`` gives the rule of the four sides (-x, +x, -y, +y); ``wall_u`` the
     velocity of each side as a moving bounce-back wall; ``inlet_u`` the inflow
@@ -126,7 +153,7 @@ class Lattice:
     """
 
     def __init__(self, nx, ny, tau, rho0=1.0, bc=(0, 0, 0, 0), wall_u=None,
-                 inlet_u=(0.0, 0.0), n_corr=10):
+                 inlet_u=(0.0, 0.0), n_corr=10, mrt=None):
         self._lib = _load()
         self.nx, self.ny, self.n_corr = int(nx), int(ny), int(n_corr)
         bc_a = (ctypes.c_int * 4)(*[int(b) for b in bc])
@@ -136,6 +163,8 @@ class Lattice:
                                        bc_a, _dp(wu), _dp(iu), self.n_corr)
         if not self._h:
             raise MemoryError("oracle lattice allocation failed")
+        if mrt is not None:
+            self._lib.ora_set_mrt(self._h, *[float(v) for v in mrt])
 
     def close(self):
         if getattr(self, "_h", None):

@@ -21,9 +21,9 @@
  *      Eqs. 37-38 without the internal-mass terms).
  *   2. One more interpolation gives the final no-slip residual r^N.
  *   3. Free bodies: Newton-Euler update in FP64 (Eqs. 37-42).
- *   4. Moments of the corrected state (Eq. 7) are recorded; BGK collision
- *      (Eq. 1 with the single-relaxation operator named in section 2.1,
- *      equilibrium of Eq. 3).
+ *   4. Moments of the corrected state (Eq. 7) are recorded; collision with
+ *      the equilibrium of Eq. 3: BGK (Eq. 1 with the single-relaxation
+ *      operator named in section 2.1) or the MRT operator of Eqs. 2, 5, 6.
  *   5. Streaming (Eq. 1) with the domain boundary rules.
  *
  * Readings of places where the paper is silent or garbled (each is listed
@@ -78,6 +78,8 @@ typedef struct {
   double wall_u[4][2];
   double inlet_u[2];
   int n_corr;
+  int mrt;                  /* 0: BGK, 1: MRT (Eqs. 2, 5, 6) */
+  double s_rate[ORA_Q];     /* diagonal of S in Eq. 6 */
   double *f;                /* [9][ny][nx], post-stream state */
   double *g;                /* streaming scratch */
   double *df;               /* spreading scratch, [9][ny][nx] */
@@ -116,6 +118,45 @@ void ora_moments(const double *p, double *rho, double *jx, double *jy) {
   *rho = ((p[0] + (p[1] + p[3])) + (p[2] + p[4])) + ((p[5] + p[7]) + (p[6] + p[8]));
   *jx = ((p[1] - p[3]) + (p[5] - p[7])) + (p[8] - p[6]);
   *jy = ((p[2] - p[4]) + (p[5] - p[7])) + (p[6] - p[8]);
+}
+
+/* Eq. 5: the transform matrix M.  Row k maps the populations to moment k:
+ * density, energy e, energy square epsilon, x-momentum, x energy flux q_x,
+ * y-momentum, y energy flux q_y, and the stress moments p_xx, p_xy. */
+static const double ora_M[ORA_Q][ORA_Q] = {
+    { 1,  1,  1,  1,  1, 1,  1,  1,  1},
+    {-4, -1, -1, -1, -1, 2,  2,  2,  2},
+    { 4, -2, -2, -2, -2, 1,  1,  1,  1},
+    { 0,  1,  0, -1,  0, 1, -1, -1,  1},
+    { 0, -2,  0,  2,  0, 1, -1, -1,  1},
+    { 0,  0,  1,  0, -1, 1,  1, -1, -1},
+    { 0,  0, -2,  0,  2, 1,  1, -1, -1},
+    { 0,  1, -1,  1, -1, 0,  0,  0,  0},
+    { 0,  0,  0,  0,  0, 1, -1,  1, -1}};
+
+void ora_mrt_matrix(double *out) {
+  for (int k = 0; k < ORA_Q; ++k)
+    for (int i = 0; i < ORA_Q; ++i) out[k * ORA_Q + i] = ora_M[k][i];
+}
+
+/* Eq. 2 at one node: ps = p - M^-1 S M (p - feq), with S = diag(s) of
+ * Eq. 6.  The rows of M are mutually orthogonal, so M^-1 = M^T N^-1 with
+ * N = diag(|row k|^2); the norms are summed from M itself. */
+void ora_mrt_collide(const double *s, const double *p, const double *feq, double *ps) {
+  double r[ORA_Q];
+  for (int k = 0; k < ORA_Q; ++k) {
+    double mk = 0.0, nk = 0.0;
+    for (int i = 0; i < ORA_Q; ++i) {
+      mk += ora_M[k][i] * (p[i] - feq[i]);
+      nk += ora_M[k][i] * ora_M[k][i];
+    }
+    r[k] = s[k] * mk / nk;
+  }
+  for (int i = 0; i < ORA_Q; ++i) {
+    double acc = 0.0;
+    for (int k = 0; k < ORA_Q; ++k) acc += ora_M[k][i] * r[k];
+    ps[i] = p[i] - acc;
+  }
 }
 
 static size_t idx(const ora_lattice *L, int i, int x, int y) {
@@ -165,6 +206,18 @@ ora_lattice *ora_create(int nx, int ny, double tau, double rho0, const int *bc,
     L->uy[k] = 0.0;
   }
   return L;
+}
+
+/* Switch the collision to MRT (Eqs. 2, 5, 6) with rates s_e, s_eps, s_q for
+ * the energy, energy-square and energy-flux moments; the stress moments
+ * relax at 1/tau (Eq. 8).  The conserved moments (density, momentum) have
+ * zero non-equilibrium part, so their rates are immaterial; they are set to
+ * 1/tau, which makes the operator BGK when every rate is 1/tau. */
+void ora_set_mrt(ora_lattice *L, double s_e, double s_eps, double s_q) {
+  double sn = 1.0 / L->tau;
+  double s[ORA_Q] = {sn, s_e, s_eps, sn, s_q, sn, s_q, sn, sn};
+  L->mrt = 1;
+  for (int k = 0; k < ORA_Q; ++k) L->s_rate[k] = s[k];
 }
 
 void ora_destroy(ora_lattice *L) {
@@ -487,7 +540,8 @@ void ora_record_moments(ora_lattice *L) {
   (void)n;
 }
 
-/* BGK collision (Eq. 1 with Omega_i = -(f_i - f_i^eq)/tau) followed by
+/* BGK collision (Eq. 1 with Omega_i = -(f_i - f_i^eq)/tau), or MRT (Eq. 2)
+ * after ora_set_mrt, followed by
  * streaming with the boundary rules:
  *   periodic: wrap;
  *   bounce-back (half-way): a population leaving through the wall returns
@@ -513,7 +567,10 @@ void ora_collide_stream(ora_lattice *L) {
         node_pops(L, L->f, x, y, p);
         ora_moments(p, &rho, &jx, &jy);
         ora_feq(rho, jx / rho, jy / rho, feq);
-        for (int i = 0; i < ORA_Q; ++i) ps[i] = p[i] - (p[i] - feq[i]) / L->tau;
+        if (L->mrt)
+          ora_mrt_collide(L->s_rate, p, feq, ps);
+        else
+          for (int i = 0; i < ORA_Q; ++i) ps[i] = p[i] - (p[i] - feq[i]) / L->tau;
       }
       for (int i = 0; i < ORA_Q; ++i) {
         int tx = x + ora_ex[i], ty = y + ora_ey[i];

@@ -40,7 +40,12 @@ struct DeviceGuard {
 void* dev_alloc(Ctx& h, size_t bytes) {
   if (bytes == 0) bytes = 16;
   void* p = nullptr;
-  if (g_alloc) {
+  if (h.pool) {
+    if (cudaMallocFromPoolAsync(&p, bytes, h.pool, h.stream) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  } else if (g_alloc) {
     p = g_alloc(bytes, h.device, (void*)h.stream, g_actx);
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -54,7 +59,8 @@ void dev_free(Ctx& h, void* p) {
   if (!p) return;
   for (size_t k = 0; k < h.allocs.size(); ++k)
     if (h.allocs[k] == p) { h.allocs.erase(h.allocs.begin() + k); break; }
-  if (g_free) g_free(p, h.device, (void*)h.stream, g_actx);
+  if (h.pool) cudaFreeAsync(p, h.stream);
+  else if (g_free) g_free(p, h.device, (void*)h.stream, g_actx);
   else cudaFree(p);
 }
 
@@ -79,6 +85,25 @@ void destroy_graphs(Ctx& h) {
   for (int p = 0; p < 2; ++p)
     for (int m = 0; m < 2; ++m)
       if (h.graph[p][m]) { cudaGraphExecDestroy(h.graph[p][m]); h.graph[p][m] = nullptr; }
+  for (int p = 0; p < 2; ++p)
+    if (h.graph_block[p]) { cudaGraphExecDestroy(h.graph_block[p]); h.graph_block[p] = nullptr; }
+}
+
+void enqueue_step(Ctx& h, int parity, bool macro, bool timing);
+
+// Capture `count` consecutive steps starting at `parity` into one graph.
+cudaError_t capture_steps(Ctx& c, int parity, int count, bool macro_last, cudaGraphExec_t* out) {
+  cudaGraph_t graph;
+  cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int j = 0; j < count; ++j)
+    enqueue_step(c, parity ^ (j & 1), macro_last && j == count - 1, false);
+  e = cudaStreamEndCapture(c.stream, &graph);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) *out = nullptr;
+  return e;
 }
 
 ibm_status check_device_flags(Ctx* h) {
@@ -275,11 +300,23 @@ ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn release, void* ctx)
 
 const char* ibm_last_error(ibm_handle h) { return h ? h->err.c_str() : t_err.c_str(); }
 
-ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
+}  // extern "C"
+
+ibm_status ibm::create_lattice(const ibm_lattice_desc* desc, ibm_handle* out, cudaMemPool_t pool) {
   if (!out) return fail(nullptr, IBM_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!desc) return fail(nullptr, IBM_ERR_INVALID, "desc is NULL");
-  const ibm_lattice_desc& d = *desc;
+  ibm_lattice_desc d = *desc;
+  if (d.collision != IBM_COLL_BGK && d.collision != IBM_COLL_MRT)
+    return fail(nullptr, IBM_ERR_INVALID, "unknown collision operator");
+  {
+    const double paper_rates[3] = {1.1, 1.25, 1.8};   // section 3: s_e, s_eps, s_q
+    for (int k = 0; k < 3; ++k) {
+      if (d.mrt_s[k] == 0.0) d.mrt_s[k] = paper_rates[k];
+      if (!is_finite(d.mrt_s[k]) || d.mrt_s[k] <= 0.0 || d.mrt_s[k] >= 2.0)
+        return fail(nullptr, IBM_ERR_INVALID, "MRT rates must lie in (0, 2)");
+    }
+  }
   if (d.nx < 4 || d.ny < 4) return fail(nullptr, IBM_ERR_INVALID, "nx and ny must be >= 4");
   if ((long long)d.nx * d.ny >= (1LL << 31) || d.ny > 65535)
     return fail(nullptr, IBM_ERR_INVALID, "lattice too large (nx*ny < 2^31, ny <= 65535)");
@@ -315,6 +352,7 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
   DeviceGuard guard(d.device);
   if (!guard.ok) { delete h; return fail(nullptr, IBM_ERR_CUDA, "cannot select the CUDA device"); }
   Ctx& c = *h;
+  c.pool = pool;
   c.desc = d;
   c.desc.delta_points = 4;
   c.device = d.device;
@@ -401,6 +439,12 @@ ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
   if (st != IBM_OK) return bail(st);
   *out = h;
   return IBM_OK;
+}
+
+extern "C" {
+
+ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
+  return ibm::create_lattice(desc, out, nullptr);
 }
 
 ibm_status ibm_add_markers(ibm_handle h, const double* xy, const double* ds, int n,
@@ -512,21 +556,33 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
       launch_band_build(c, c.stream);
       c.band_valid = true;
     }
-    for (int k = 0; k < nsteps; ++k) {
+    const bool want_macro = !(flags & IBM_STEP_NO_MACRO);
+    for (int k = 0; k < nsteps;) {
       const int parity = c.parity;
-      const int macro = (k == nsteps - 1 && !(flags & IBM_STEP_NO_MACRO)) ? 1 : 0;
+      // whole blocks of steps that write no output fields go as one graph
+      const int plain = nsteps - k - (want_macro ? 1 : 0);
+      if (use_graph && plain >= kBlockSteps) {
+        if (!c.graph_block[parity]) {
+          cudaError_t e = capture_steps(c, parity, kBlockSteps, false, &c.graph_block[parity]);
+          if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, IBM_ERR_CUDA, std::string("capturing a block of steps: ") + cudaGetErrorString(e));
+          }
+        }
+        IBM_CK(h, cudaGraphLaunch(c.graph_block[parity], c.stream));
+        c.launches += (long long)kBlockSteps * kernels_per_step(c);
+        c.steps += kBlockSteps;
+        k += kBlockSteps;
+        continue;
+      }
+      const int macro = (k == nsteps - 1 && want_macro) ? 1 : 0;
+      ++k;
       if (use_graph) {
         if (!c.graph[parity][macro]) {
-          cudaGraph_t graph;
-          IBM_CK(h, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
-          enqueue_step(c, parity, macro != 0, false);
-          IBM_CK(h, cudaStreamEndCapture(c.stream, &graph));
-          cudaError_t e = cudaGraphInstantiate(&c.graph[parity][macro], graph, 0);
-          cudaGraphDestroy(graph);
+          cudaError_t e = capture_steps(c, parity, 1, macro != 0, &c.graph[parity][macro]);
           if (e != cudaSuccess) {
-            c.graph[parity][macro] = nullptr;
             cudaGetLastError();
-            return fail(h, IBM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            return fail(h, IBM_ERR_CUDA, std::string("capturing a step: ") + cudaGetErrorString(e));
           }
         }
         IBM_CK(h, cudaGraphLaunch(c.graph[parity][macro], c.stream));

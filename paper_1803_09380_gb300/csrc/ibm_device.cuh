@@ -91,6 +91,8 @@ struct Geom {
 template <class R>
 struct StepConsts {
   R omega;                  // 1 / tau
+  int mrt;                  // 0: BGK, 1: MRT (Eqs. 2, 5, 6)
+  R mrt_k[3];               // (s_e - 1/tau)/36, (s_eps - 1/tau)/36, (s_q - 1/tau)/12
   R wall[4][9];             // 6 w_i rho0 (e_i . U_wall[side])
   R feq_in[9];              // inlet equilibrium f^eq(rho0, U_in)
   R rho0;

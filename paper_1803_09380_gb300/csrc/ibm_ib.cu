@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
 
 // Collide+stream of the 32-node row segments that hold band nodes, after
 // the correction kernel has corrected them: one warp per segment.
-template <int P, int PAR, bool MACRO>
+template <int P, int PAR, bool MACRO, bool MRT>
 __global__ void __launch_bounds__(256) k_band_collide(Geom g, StepConsts<typename Prec<P>::R> c,
                                                       typename Prec<P>::S* __restrict__ A,
                                                       typename Prec<P>::R* __restrict__ mac,
@@ -647,8 +647,8 @@ __global__ void __launch_bounds__(256) k_band_collide(Geom g, StepConsts<typenam
     const int seg = seglist[k];
     const int y = seg / nseg_x, x = (seg % nseg_x) * kSegW + lane;
     if (x >= g.nx) continue;
-    if (PAR == 0) even_node<P, MACRO>(g, c, A, mac, x, y);
-    else odd_node<P, MACRO>(g, c, A, mac, x, y);
+    if (PAR == 0) even_node<P, MACRO, MRT>(g, c, A, mac, x, y);
+    else odd_node<P, MACRO, MRT>(g, c, A, mac, x, y);
   }
 }
 
@@ -761,6 +761,18 @@ void launch_band_build(const Ctx& h, cudaStream_t s) {
   else band_build_t<float>(h, s);
 }
 
+template <int P, bool MRT>
+static void launch_band_collide(dim3 g2, dim3 b2, cudaStream_t s, int prio, const IbArgs<P>& a,
+                                const int* ctr, int parity, bool macro) {
+  if (parity == 0) {
+    if (macro) launch_prio(k_band_collide<P, 0, true, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+    else launch_prio(k_band_collide<P, 0, false, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+  } else {
+    if (macro) launch_prio(k_band_collide<P, 1, true, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+    else launch_prio(k_band_collide<P, 1, false, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+  }
+}
+
 template <int P>
 static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   typedef typename Prec<P>::S S;
@@ -808,13 +820,8 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
     const int need = (h.segcap * kSegW + 255) / 256;
     const dim3 g2(need < 8 * h.ib_grid_max ? (need > 0 ? need : 1) : 8 * h.ib_grid_max), b2(256);
     const int* ctr = a.ctr;
-    if (parity == 0) {
-      if (macro) launch_prio(k_band_collide<P, 0, true>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
-      else launch_prio(k_band_collide<P, 0, false>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
-    } else {
-      if (macro) launch_prio(k_band_collide<P, 1, true>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
-      else launch_prio(k_band_collide<P, 1, false>, g2, b2, s, h.ib_prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
-    }
+    if (a.c.mrt) launch_band_collide<P, true>(g2, b2, s, h.ib_prio, a, ctr, parity, macro);
+    else launch_band_collide<P, false>(g2, b2, s, h.ib_prio, a, ctr, parity, macro);
   }
 }
 

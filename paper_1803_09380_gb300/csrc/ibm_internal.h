@@ -34,6 +34,7 @@ struct alignas(2 * sizeof(R) > 8 ? 16 : 8) Ent {
 
 constexpr int kIbThreads = 256;                  // threads per correction-loop CTA
 constexpr int kGCap = 64;                        // coupled markers per marker (G row)
+constexpr int kBlockSteps = 8;       // steps per multi-step graph (even: parity returns)
 constexpr int kForceChunk = 128;                 // markers per partial force sum
 constexpr int kSmallIbMarkers = 512;             // up to this many markers: one correction CTA
 constexpr long long kBarrierCycles = 4000000000LL; // ~2 s at 2 GHz: grid-barrier wait limit
@@ -60,6 +61,7 @@ struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaMemPool_t pool = nullptr;  // set: stream-ordered allocations from this pool
   cudaStream_t ib_stream = nullptr;   // high-priority stream of the correction loop
   int ib_prio = 0;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -115,6 +117,7 @@ struct Ctx {
 
   // CUDA graphs of one step, per parity and macro flag
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphExec_t graph_block[2] = {nullptr, nullptr};   // kBlockSteps steps from parity p
 
   // kernel timing: kEventsPerStep events per timed step
   std::vector<cudaEvent_t> ev;
@@ -158,6 +161,10 @@ StepConsts<R> make_consts(const Ctx& h) {
   StepConsts<R> c;
   const ibm_lattice_desc& d = h.desc;
   c.omega = (R)(1.0 / d.tau);
+  c.mrt = d.collision == IBM_COLL_MRT;
+  c.mrt_k[0] = (R)((d.mrt_s[0] - 1.0 / d.tau) / 36.0);
+  c.mrt_k[1] = (R)((d.mrt_s[1] - 1.0 / d.tau) / 36.0);
+  c.mrt_k[2] = (R)((d.mrt_s[2] - 1.0 / d.tau) / 12.0);
   c.rho0 = (R)d.rho0;
   c.inlet_u[0] = (R)d.inlet_u[0];
   c.inlet_u[1] = (R)d.inlet_u[1];
@@ -193,6 +200,10 @@ inline void launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStr
 
 // ibm_api.cu
 void set_thread_error(const char* msg);
+// ibm_create_lattice with an optional memory pool: when pool is not NULL
+// every device allocation of the handle is stream-ordered on its stream
+// (no device-wide synchronisation when the handle is destroyed).
+ibm_status create_lattice(const ibm_lattice_desc* desc, ibm_handle* out, cudaMemPool_t pool);
 
 // ibm_lbm.cu
 void launch_collide_stream(const Ctx& h, int parity, bool macro, int mode, cudaStream_t s);

@@ -1,7 +1,8 @@
-// ibm_k1.cuh -- one node of the fused BGK collide + AA-pattern stream
-// (arXiv 1803.09380, Eq. 1 with the single-relaxation operator of section
-// 2.1, equilibrium of Eq. 3, moments of Eq. 7), shared by the collide+stream
-// kernels and by the correction-loop kernel, which runs the band segments.
+// ibm_k1.cuh -- one node of the fused collide + AA-pattern stream
+// (arXiv 1803.09380, Eq. 1 with either the single-relaxation operator of
+// section 2.1 or the MRT operator of Eqs. 2, 5, 6; equilibrium of Eq. 3,
+// moments of Eq. 7), shared by the collide+stream kernels and by the
+// band collide kernel.
 #pragma once
 
 #include "ibm_internal.h"
@@ -21,6 +22,55 @@ __device__ __forceinline__ void bgk(const R* p, R* ps, R& rho, R& jx, R& jy, R o
   }
 }
 
+// MRT (Eq. 2) written as BGK at the stress rate s_nu = 1/tau plus the
+// difference on the energy (e), energy-square (eps) and energy-flux (q_x,
+// q_y) moments, rows 1, 2, 4, 6 of Eq. 5:
+//   f_i' = f_i - s_nu d_i - sum_k (s_k - s_nu) / |M_k|^2  M_ki (M_k . d),
+// d = f - f^eq.  The conserved moments of d vanish, so their rates (taken
+// as s_nu) do not enter.  c.mrt_k holds (s_e - s_nu)/36, (s_eps - s_nu)/36
+// and (s_q - s_nu)/12.
+template <class R>
+__device__ __forceinline__ void mrt(const R* p, R* ps, R& rho, R& jx, R& jy,
+                                    const StepConsts<R>& c) {
+  moments9(p, rho, jx, jy);
+  R inv = R(1) / rho;
+  R ux = jx * inv, uy = jy * inv;
+  R pxx = jx * ux, pxy = jx * uy, pyy = jy * uy;
+  R d[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) d[i] = p[i] - feq_i<R>(i, rho, jx, jy, pxx, pxy, pyy);
+  const R s14 = (d[1] + d[3]) + (d[2] + d[4]);
+  const R s58 = (d[5] + d[7]) + (d[6] + d[8]);
+  const R me = c.mrt_k[0] * ((s58 + s58) - s14 - R(4) * d[0]);
+  const R mp = c.mrt_k[1] * (R(4) * d[0] - (s14 + s14) + s58);
+  const R a57 = d[5] - d[7];
+  const R qx = c.mrt_k[2] * (R(2) * (d[3] - d[1]) + a57 + (d[8] - d[6]));
+  const R qy = c.mrt_k[2] * (R(2) * (d[4] - d[2]) + a57 + (d[6] - d[8]));
+  const R cax = -me - (mp + mp);          // axis directions share e, eps parts
+  const R cdg = (me + me) + mp;           // diagonal directions
+  const R w = c.omega;
+  ps[0] = p[0] - (w * d[0] + R(4) * (mp - me));
+  ps[1] = p[1] - (w * d[1] + (cax - (qx + qx)));
+  ps[2] = p[2] - (w * d[2] + (cax - (qy + qy)));
+  ps[3] = p[3] - (w * d[3] + (cax + (qx + qx)));
+  ps[4] = p[4] - (w * d[4] + (cax + (qy + qy)));
+  ps[5] = p[5] - (w * d[5] + (cdg + qx + qy));
+  ps[6] = p[6] - (w * d[6] + (cdg - qx + qy));
+  ps[7] = p[7] - (w * d[7] + (cdg - qx - qy));
+  ps[8] = p[8] - (w * d[8] + (cdg + qx - qy));
+}
+
+// The collision of the lattice: the operator is a template parameter of
+// the kernels, so the BGK kernels carry no trace of the MRT arithmetic.
+template <class R, bool MRT>
+__device__ __forceinline__ void collide(const R* p, R* ps, R& rho, R& jx, R& jy,
+                                        const StepConsts<R>& c) {
+  if constexpr (MRT)
+    mrt<R>(p, ps, rho, jx, jy, c);
+  else
+    bgk<R>(p, ps, rho, jx, jy, c.omega);
+}
+
 template <class R>
 __device__ __forceinline__ void write_macro(R* mac, long long n, long long k, R rho, R jx, R jy) {
   R inv = R(1) / rho;
@@ -31,7 +81,7 @@ __device__ __forceinline__ void write_macro(R* mac, long long n, long long k, R 
 
 // ------------------------------------------------------------------ even step
 // Reads A[i][x], writes f*_i to A[opp(i)][x]: purely node-local.
-template <int P, bool MACRO>
+template <int P, bool MACRO, bool MRT>
 __device__ __forceinline__ void even_node(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                           typename Prec<P>::S* __restrict__ A,
                                           typename Prec<P>::R* __restrict__ mac, int x, int y) {
@@ -45,7 +95,7 @@ __device__ __forceinline__ void even_node(const Geom& g, const StepConsts<typena
     for (int i = 0; i < 9; ++i) ps[i] = c.feq_in[i];
     rho = c.rho0; jx = c.rho0 * c.inlet_u[0]; jy = c.rho0 * c.inlet_u[1];
   } else {
-    bgk<R>(p, ps, rho, jx, jy, c.omega);
+    collide<R, MRT>(p, ps, rho, jx, jy, c);
   }
   if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x, rho, jx, jy);
 #pragma unroll
@@ -55,7 +105,7 @@ __device__ __forceinline__ void even_node(const Geom& g, const StepConsts<typena
 // ------------------------------------------------------------------ odd step
 // Boundary path for one or two nodes (two when x = nx-2 before an outlet:
 // those columns share slots, so one thread reads both before writing).
-template <int P, bool MACRO>
+template <int P, bool MACRO, bool MRT>
 __device__ void odd_boundary(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                              typename Prec<P>::S* A, typename Prec<P>::R* mac, int x, int y) {
   typedef typename Prec<P>::R R;
@@ -73,7 +123,7 @@ __device__ void odd_boundary(const Geom& g, const StepConsts<typename Prec<P>::R
       for (int i = 0; i < 9; ++i) ps[q][i] = c.feq_in[i];
       rho = c.rho0; jx = c.rho0 * c.inlet_u[0]; jy = c.rho0 * c.inlet_u[1];
     } else {
-      bgk<R>(p, ps[q], rho, jx, jy, c.omega);
+      collide<R, MRT>(p, ps[q], rho, jx, jy, c);
     }
     if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + xq, rho, jx, jy);
   }
@@ -89,13 +139,13 @@ __device__ void odd_boundary(const Geom& g, const StepConsts<typename Prec<P>::R
   }
 }
 
-template <int P, bool MACRO>
+template <int P, bool MACRO, bool MRT>
 __device__ __forceinline__ void odd_node(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                          typename Prec<P>::S* __restrict__ A,
                                          typename Prec<P>::R* __restrict__ mac, int x, int y) {
   typedef typename Prec<P>::R R;
   if (needs_boundary_path(g, x, y)) {
-    odd_boundary<P, MACRO>(g, c, A, mac, x, y);
+    odd_boundary<P, MACRO, MRT>(g, c, A, mac, x, y);
     return;
   }
   // Interior or periodic node: neighbours by wrap-around (a no-op unless the
@@ -109,7 +159,7 @@ __device__ __forceinline__ void odd_node(const Geom& g, const StepConsts<typenam
     const int sy = cy(i) > 0 ? ym : (cy(i) < 0 ? yp : y);
     p[i] = Prec<P>::ld(A[opp(i) * g.plane + (long long)sy * g.nxp + sx], opp(i));
   }
-  bgk<R>(p, ps, rho, jx, jy, c.omega);
+  collide<R, MRT>(p, ps, rho, jx, jy, c);
   if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x, rho, jx, jy);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -158,7 +208,7 @@ __device__ __forceinline__ S shfl_down1(S v) { return __shfl_down_sync(0xfffffff
 
 // Collide VEC nodes whose pre-collision populations are p[i][k]
 // (arithmetic type), in place, writing macros if asked.
-template <int P, bool MACRO, int VEC>
+template <int P, bool MACRO, bool MRT, int VEC>
 __device__ __forceinline__ void collide_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                             typename Prec<P>::R (&p)[9][VEC],
                                             typename Prec<P>::R* __restrict__ mac, int x0, int y) {
@@ -173,7 +223,7 @@ __device__ __forceinline__ void collide_vec(const Geom& g, const StepConsts<type
       for (int i = 0; i < 9; ++i) qs[i] = c.feq_in[i];
       rho = c.rho0; jx = c.rho0 * c.inlet_u[0]; jy = c.rho0 * c.inlet_u[1];
     } else {
-      bgk<R>(q, qs, rho, jx, jy, c.omega);
+      collide<R, MRT>(q, qs, rho, jx, jy, c);
     }
     if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x0 + k, rho, jx, jy);
 #pragma unroll
@@ -183,7 +233,7 @@ __device__ __forceinline__ void collide_vec(const Geom& g, const StepConsts<type
 
 // Even step for the VEC nodes x0.. of row y (all inside the lattice):
 // aligned vector loads of A[i], vector stores to A[opp(i)].
-template <int P, bool MACRO>
+template <int P, bool MACRO, bool MRT>
 __device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                          typename Prec<P>::S* __restrict__ A,
                                          typename Prec<P>::R* __restrict__ mac, int x0, int y) {
@@ -198,7 +248,7 @@ __device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typenam
 #pragma unroll
     for (int k = 0; k < VEC; ++k) p[i][k] = Prec<P>::ld(v.v[k], i);
   }
-  collide_vec<P, MACRO, VEC>(g, c, p, mac, x0, y);
+  collide_vec<P, MACRO, MRT, VEC>(g, c, p, mac, x0, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     SVec<S, VEC> v;
@@ -216,7 +266,7 @@ __device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typenam
 // neighbouring span are read or written with scalar accesses by the thread
 // whose node owns the slot (lane 0 and lane 31), so spans never write each
 // other's slots.
-template <int P, bool MACRO>
+template <int P, bool MACRO, bool MRT>
 __device__ __forceinline__ void odd_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                         typename Prec<P>::S* __restrict__ A,
                                         typename Prec<P>::R* __restrict__ mac, int x0, int y, int lane) {
@@ -250,7 +300,7 @@ __device__ __forceinline__ void odd_vec(const Geom& g, const StepConsts<typename
       p[i][VEC - 1] = Prec<P>::ld(right, sl);
     }
   }
-  collide_vec<P, MACRO, VEC>(g, c, p, mac, x0, y);
+  collide_vec<P, MACRO, MRT, VEC>(g, c, p, mac, x0, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int ty = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);

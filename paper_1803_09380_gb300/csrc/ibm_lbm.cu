@@ -33,7 +33,7 @@ namespace ibm {
 // Even step: per lane, aligned vectors (ragged row ends node by node).  Odd
 // step: spans without boundary, ragged or band nodes take the vector path;
 // the others go node by node through the boundary-aware path.
-template <int P, int PAR, bool MACRO, int MODE>
+template <int P, int PAR, bool MACRO, int MODE, bool MRT>
 __global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
                                                         typename Prec<P>::S* __restrict__ A,
                                                         typename Prec<P>::R* __restrict__ mac,
@@ -48,9 +48,9 @@ __global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typen
   if (PAR == 0) {
     if (flagged || x0 >= g.nx) return;
     if (x0 + VEC <= g.nx) {
-      even_vec<P, MACRO>(g, c, A, mac, x0, y);
+      even_vec<P, MACRO, MRT>(g, c, A, mac, x0, y);
     } else {
-      for (int x = x0; x < g.nx; ++x) even_node<P, MACRO>(g, c, A, mac, x, y);
+      for (int x = x0; x < g.nx; ++x) even_node<P, MACRO, MRT>(g, c, A, mac, x, y);
     }
     return;
   }
@@ -63,11 +63,11 @@ __global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typen
       const int x = x0 + k;
       if (x >= g.nx) break;
       if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) continue;
-      odd_node<P, MACRO>(g, c, A, mac, x, y);
+      odd_node<P, MACRO, MRT>(g, c, A, mac, x, y);
     }
     return;
   }
-  odd_vec<P, MACRO>(g, c, A, mac, x0, y, lane);
+  odd_vec<P, MACRO, MRT>(g, c, A, mac, x0, y, lane);
 }
 
 // ------------------------------------------------------------------ fields
@@ -155,7 +155,7 @@ __global__ void k_macro_to_double(long long n, const R* __restrict__ mac, double
 // ------------------------------------------------------------------ launchers
 static dim3 row_grid(const Geom& g, int bs) { return dim3((g.nx + bs - 1) / bs, g.ny); }
 
-template <int P, int PAR, bool MACRO>
+template <int P, int PAR, bool MACRO, bool MRT>
 static void launch_k1(const Ctx& h, const StepConsts<typename Prec<P>::R>& c, int mode, cudaStream_t s) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
@@ -165,10 +165,10 @@ static void launch_k1(const Ctx& h, const StepConsts<typename Prec<P>::R>& c, in
   const int warps_per_row = (h.geom.nx + 32 * VEC - 1) / (32 * VEC);
   const dim3 grid((warps_per_row + 7) / 8, h.geom.ny);
   if (mode == K1_MAIN) {
-    k_collide_stream<P, PAR, MACRO, K1_MAIN><<<grid, 256, 0, s>>>(
+    k_collide_stream<P, PAR, MACRO, K1_MAIN, MRT><<<grid, 256, 0, s>>>(
         h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   } else {
-    k_collide_stream<P, PAR, MACRO, K1_ALL><<<grid, 256, 0, s>>>(
+    k_collide_stream<P, PAR, MACRO, K1_ALL, MRT><<<grid, 256, 0, s>>>(
         h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   }
 }
@@ -177,12 +177,22 @@ template <int P>
 static void launch_collide_stream_t(const Ctx& h, int parity, bool macro, int mode, cudaStream_t s) {
   typedef typename Prec<P>::R R;
   StepConsts<R> c = make_consts<R>(h);
-  if (parity == 0) {
-    if (macro) launch_k1<P, 0, true>(h, c, mode, s);
-    else launch_k1<P, 0, false>(h, c, mode, s);
+  if (c.mrt) {
+    if (parity == 0) {
+      if (macro) launch_k1<P, 0, true, true>(h, c, mode, s);
+      else launch_k1<P, 0, false, true>(h, c, mode, s);
+    } else {
+      if (macro) launch_k1<P, 1, true, true>(h, c, mode, s);
+      else launch_k1<P, 1, false, true>(h, c, mode, s);
+    }
   } else {
-    if (macro) launch_k1<P, 1, true>(h, c, mode, s);
-    else launch_k1<P, 1, false>(h, c, mode, s);
+    if (parity == 0) {
+      if (macro) launch_k1<P, 0, true, false>(h, c, mode, s);
+      else launch_k1<P, 0, false, false>(h, c, mode, s);
+    } else {
+      if (macro) launch_k1<P, 1, true, false>(h, c, mode, s);
+      else launch_k1<P, 1, false, false>(h, c, mode, s);
+    }
   }
 }
 

@@ -48,8 +48,8 @@ struct CaseRec {
   int ib_ctas = 1;
   ibm_handle h = nullptr;
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
-  bool inflight = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};   // ring of chunk-completion events
+  int head = 0, inflight = 0;
   double t_submit = 0.0, t_done = 0.0;
   int state = CASE_PENDING;
   ibm_status status = IBM_OK;
@@ -75,6 +75,17 @@ double case_bytes(const ibm_lattice_desc& d, int M, int nb) {
   return b + (1 << 20);
 }
 
+// Correction-loop CTAs of a served case: one CTA per `per_cta` markers, at
+// most one per SM.  Fewer CTAs than the stand-alone default (one per SM)
+// keep each case's grid barrier cheap and let many cases' correction
+// kernels be resident at once.
+constexpr int kServeMarkersPerCta = 512;
+int server_ib_ctas(int M, int sms, int per_cta) {
+  if (M == 0) return 0;
+  if (per_cta <= 0) per_cta = kServeMarkersPerCta;
+  return std::max(1, std::min(sms, (M + per_cta - 1) / per_cta));
+}
+
 }  // namespace
 
 struct ibm_server_s {
@@ -87,6 +98,7 @@ struct ibm_server_s {
   std::vector<long long> active;
   std::vector<cudaStream_t> streams;       // idle streams for reuse
   std::vector<cudaEvent_t> events;
+  cudaMemPool_t pool = nullptr;
   double bytes_in_use = 0.0;
   int ctas_in_use = 0;
   long long next_id = 1;
@@ -94,6 +106,7 @@ struct ibm_server_s {
   std::vector<double> tts_ms;
   double t_first = -1.0, t_last = 0.0;
   double lattice_updates = 0.0;
+  double t_admit = 0.0, t_launch = 0.0, t_harvest = 0.0;   // host seconds
   std::string err;
 };
 
@@ -115,7 +128,8 @@ void case_fail(ibm_server s, CaseRec* c, ibm_status st, const char* where) {
 void release_device(ibm_server s, CaseRec* c) {
   if (c->h) { ibm_destroy(c->h); c->h = nullptr; }
   if (c->stream) { s->streams.push_back(c->stream); c->stream = nullptr; }
-  if (c->done) { s->events.push_back(c->done); c->done = nullptr; }
+  for (auto& e : c->ev)
+    if (e) { s->events.push_back(e); e = nullptr; }
   s->bytes_in_use -= c->bytes;
   s->ctas_in_use -= c->ib_ctas;
   s->active.erase(std::remove(s->active.begin(), s->active.end(), c->id), s->active.end());
@@ -128,11 +142,20 @@ ibm_status launch_chunk(ibm_server s, CaseRec* c) {
   ibm_status st = ibm_step(c->h, n, flags);
   if (st != IBM_OK) return st;
   c->remaining -= n;
-  if (cudaEventRecord(c->done, c->stream) != cudaSuccess) {
+  if (cudaEventRecord(c->ev[(c->head + c->inflight) & 1], c->stream) != cudaSuccess) {
     cudaGetLastError();
     return IBM_ERR_CUDA;
   }
-  c->inflight = true;
+  c->inflight++;
+  return IBM_OK;
+}
+
+// Keep up to two chunks of the case queued on its stream.
+ibm_status top_up(ibm_server s, CaseRec* c) {
+  while (c->remaining > 0 && c->inflight < 2) {
+    ibm_status st = launch_chunk(s, c);
+    if (st != IBM_OK) return st;
+  }
   return IBM_OK;
 }
 
@@ -143,17 +166,22 @@ ibm_status admit(ibm_server s, CaseRec* c) {
     c->stream = nullptr;
     return IBM_ERR_CUDA;
   }
-  if (!s->events.empty()) { c->done = s->events.back(); s->events.pop_back(); }
-  else if (cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    c->done = nullptr;
-    return IBM_ERR_CUDA;
+  for (auto& e : c->ev) {
+    if (!s->events.empty()) { e = s->events.back(); s->events.pop_back(); }
+    else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      e = nullptr;
+      return IBM_ERR_CUDA;
+    }
   }
+  c->head = 0;
+  c->inflight = 0;
   ibm_lattice_desc d = c->desc;
   d.cuda_stream = c->stream;
   d.device = s->desc.device;
-  ibm_status st = ibm_create_lattice(&d, &c->h);
+  ibm_status st = ibm::create_lattice(&d, &c->h, s->pool);
   if (st != IBM_OK) return st;
+  if (c->ib_ctas > 0 && (st = ibm_set_option(c->h, IBM_OPT_IB_CTAS, c->ib_ctas)) != IBM_OK) return st;
   size_t off = 0;
   for (size_t b = 0; b < c->bodies.size(); ++b) {
     st = ibm_add_markers(c->h, c->xy.data() + 2 * off, c->has_ds ? c->ds.data() + off : nullptr,
@@ -161,7 +189,7 @@ ibm_status admit(ibm_server s, CaseRec* c) {
     if (st != IBM_OK) return st;
     off += c->nmark[b];
   }
-  return launch_chunk(s, c);
+  return top_up(s, c);
 }
 
 ibm_status harvest(ibm_server s, CaseRec* c) {
@@ -216,6 +244,23 @@ ibm_status ibm_server_create(const ibm_server_desc* desc, ibm_server* out) {
   cudaGetLastError();
   s->budget = desc->max_device_bytes > 0 ? desc->max_device_bytes : 0.8 * (double)free_b;
   s->cta_budget = desc->ib_cta_budget > 0 ? desc->ib_cta_budget : 2 * s->sms;
+  {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = desc->device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      cudaSetDevice(prev);
+      delete s;
+      return sfail(nullptr, IBM_ERR_CUDA, "cannot create the server's memory pool");
+    }
+    // keep freed memory cached up to the budget: retiring a case returns
+    // nothing to the driver
+    unsigned long long keep = (unsigned long long)s->budget;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaGetLastError();
+  }
   cudaSetDevice(prev);
   *out = s;
   return IBM_OK;
@@ -241,7 +286,7 @@ ibm_status ibm_server_submit(ibm_server s, const ibm_case_desc* c, long long* ca
     r->xy.assign(c->xy ? c->xy : nullptr, c->xy ? c->xy + 2 * (size_t)M : nullptr);
     if (c->ds) { r->ds.assign(c->ds, c->ds + M); r->has_ds = true; }
     r->bytes = case_bytes(c->lattice, M, c->nbodies);
-    r->ib_ctas = M == 0 ? 0 : (M <= kSmallIbMarkers ? 1 : s->sms);
+    r->ib_ctas = server_ib_ctas(M, s->sms, s->desc.ib_markers_per_cta);
     r->t_submit = now_s();
     if (s->t_first < 0) s->t_first = r->t_submit;
     s->cases[r->id] = r;
@@ -264,22 +309,30 @@ ibm_status ibm_server_progress(ibm_server s, int* completed) {
   std::vector<long long> act = s->active;
   for (long long id : act) {
     CaseRec* c = s->cases[id];
-    if (!c->inflight) continue;
-    const cudaError_t q = cudaEventQuery(c->done);
-    if (q == cudaErrorNotReady) continue;
-    c->inflight = false;
-    if (q != cudaSuccess) {
+    cudaError_t q = cudaSuccess;
+    while (c->inflight > 0) {
+      q = cudaEventQuery(c->ev[c->head]);
+      if (q != cudaSuccess) break;
+      c->head ^= 1;
+      c->inflight--;
+    }
+    if (q != cudaSuccess && q != cudaErrorNotReady) {
       cudaGetLastError();
       case_fail(s, c, IBM_ERR_CUDA, "chunk");
       release_device(s, c);
       continue;
     }
     if (c->remaining > 0) {
-      ibm_status st = launch_chunk(s, c);
+      const double t0 = now_s();
+      ibm_status st = top_up(s, c);
+      s->t_launch += now_s() - t0;
       if (st != IBM_OK) { case_fail(s, c, st, "ibm_step"); release_device(s, c); }
       continue;
     }
+    if (c->inflight > 0) continue;
+    const double t0 = now_s();
     ibm_status st = harvest(s, c);
+    s->t_harvest += now_s() - t0;
     if (st != IBM_OK) {
       case_fail(s, c, st, "ibm_read_fields");
     } else {
@@ -305,7 +358,9 @@ ibm_status ibm_server_progress(ibm_server s, int* completed) {
     s->active.push_back(c->id);
     s->bytes_in_use += c->bytes;
     s->ctas_in_use += c->ib_ctas;
+    const double t0 = now_s();
     ibm_status st = admit(s, c);
+    s->t_admit += now_s() - t0;
     if (st != IBM_OK) { case_fail(s, c, st, "admission"); release_device(s, c); }
   }
   cudaSetDevice(prev);
@@ -369,6 +424,9 @@ ibm_status ibm_server_get_stats(ibm_server s, ibm_server_stats* out) {
   r.active = (long long)s->active.size();
   r.pending = (long long)s->pending.size();
   r.device_bytes = s->bytes_in_use;
+  r.host_admit_s = s->t_admit;
+  r.host_launch_s = s->t_launch;
+  r.host_harvest_s = s->t_harvest;
   if (!s->tts_ms.empty()) {
     std::vector<double> t = s->tts_ms;
     std::sort(t.begin(), t.end());
@@ -401,13 +459,16 @@ ibm_status ibm_server_destroy(ibm_server s) {
   cudaSetDevice(s->desc.device);
   for (auto& kv : s->cases) {
     CaseRec* c = kv.second;
-    if (c->h) ibm_destroy(c->h);
-    if (c->stream) cudaStreamDestroy(c->stream);
-    if (c->done) cudaEventDestroy(c->done);
+    if (c->h) ibm_destroy(c->h);      // frees are ordered on the case's stream
+    if (c->stream) { cudaStreamSynchronize(c->stream); cudaStreamDestroy(c->stream); }
+    for (cudaEvent_t e : c->ev)
+      if (e) cudaEventDestroy(e);
     delete c;
   }
-  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  for (cudaStream_t st : s->streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
   for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+  if (s->pool) cudaMemPoolDestroy(s->pool);
+  cudaGetLastError();
   cudaSetDevice(prev);
   delete s;
   return IBM_OK;

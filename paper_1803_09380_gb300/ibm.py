@@ -16,11 +16,19 @@ import numpy as np
 
 from . import build as _build
 
+# Kernels on different streams overlap only when they reach the GPU through
+# different hardware work queues; CUDA gives a process 8 unless this is set
+# before the process creates its CUDA context.  The serving layer keeps
+# dozens of lattices (two streams each) resident, so ask for 32.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 IBM_OK, IBM_ERR_INVALID, IBM_ERR_NOMEM, IBM_ERR_CUDA = 0, 1, 2, 3
 IBM_ERR_BOUNDS, IBM_ERR_DIVERGED, IBM_ERR_TIMEOUT, IBM_WARN_NOT_CONVERGED = 4, 5, 6, 7
 IBM_FP64, IBM_FP32, IBM_FP16_DEV, IBM_BF16_DEV = 0, 1, 2, 3
 PERIODIC, BOUNCEBACK, FREESLIP, INLET_EQ, OUTLET_ZEROGRAD = 0, 1, 2, 3, 4
 BODY_FIXED, BODY_PRESCRIBED, BODY_FREE = 0, 1, 2
+COLL_BGK, COLL_MRT = 0, 1
+PAPER_MRT_RATES = (1.1, 1.25, 1.8)   # s_e, s_eps, s_q of section 3
 FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_F = 1, 2, 3, 4
 FIELD_BODIES, FIELD_RESIDUAL, FIELD_MARKERS, FIELD_MACRO_INIT = 5, 6, 7, 8
 STEP_DEFAULT, STEP_NO_GRAPH, STEP_TIME_KERNELS, STEP_NO_MACRO = 0, 1, 2, 4
@@ -54,7 +62,8 @@ class LatticeDesc(ctypes.Structure):
                 ("wall_u", (ctypes.c_double * 2) * 4), ("inlet_u", ctypes.c_double * 2),
                 ("n_corr", ctypes.c_int), ("corr_tol", ctypes.c_double),
                 ("delta_points", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("collision", ctypes.c_int),
+                ("mrt_s", ctypes.c_double * 3)]
 
 
 class BodyDesc(ctypes.Structure):
@@ -68,7 +77,7 @@ class BodyDesc(ctypes.Structure):
 class ServerDesc(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_device_bytes", ctypes.c_double),
                 ("max_active", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
-                ("ib_cta_budget", ctypes.c_int)]
+                ("ib_cta_budget", ctypes.c_int), ("ib_markers_per_cta", ctypes.c_int)]
 
 
 class CaseDesc(ctypes.Structure):
@@ -84,7 +93,9 @@ class ServerStats(ctypes.Structure):
                 ("failed", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
                 ("p95_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double),
-                ("mlups", ctypes.c_double), ("device_bytes", ctypes.c_double)]
+                ("mlups", ctypes.c_double), ("device_bytes", ctypes.c_double),
+                ("host_admit_s", ctypes.c_double), ("host_launch_s", ctypes.c_double),
+                ("host_harvest_s", ctypes.c_double)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
@@ -198,19 +209,13 @@ def use_torch_allocator() -> bool:
 
 
 def ibm_create_lattice(nx, ny, tau, rho0=1.0, prec="fp32", bc=(PERIODIC,) * 4, wall_u=None,
-                       inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, stream=None, device=0):
-    """Create a lattice in the rest equilibrium; returns an opaque handle."""
+                       inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, stream=None, device=0,
+                       mrt=None):
+    """Create a lattice in the rest equilibrium; returns an opaque handle.
+    ``mrt``: None for BGK, else the rates (s_e, s_eps, s_q) of Eq. 6 (a 0
+    entry takes the value of section 3)."""
     lib = load()
-    d = LatticeDesc()
-    d.nx, d.ny, d.tau, d.rho0 = int(nx), int(ny), float(tau), float(rho0)
-    d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
-    for s in range(4):
-        d.bc[s] = int(bc[s])
-    wu = np.zeros(8) if wall_u is None else np.asarray(wall_u, dtype=np.float64).reshape(8)
-    for s in range(4):
-        d.wall_u[s][0], d.wall_u[s][1] = float(wu[2 * s]), float(wu[2 * s + 1])
-    d.inlet_u[0], d.inlet_u[1] = float(inlet_u[0]), float(inlet_u[1])
-    d.n_corr, d.corr_tol, d.delta_points = int(n_corr), float(corr_tol), 4
+    d = _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol, mrt)
     d.cuda_stream = stream
     d.device = int(device)
     h = ctypes.c_void_p()
@@ -335,16 +340,16 @@ def _scheck(st: int, srv, where: str) -> int:
     raise IBMError(st, where, msg)
 
 
-def ibm_server_create(device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=100,
-                      ib_cta_budget=0):
+def ibm_server_create(device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=32,
+                      ib_cta_budget=0, ib_markers_per_cta=0):
     d = ServerDesc(int(device), float(max_device_bytes), int(max_active), int(steps_per_launch),
-                   int(ib_cta_budget))
+                   int(ib_cta_budget), int(ib_markers_per_cta))
     srv = ctypes.c_void_p()
     _scheck(load().ibm_server_create(ctypes.byref(d), ctypes.byref(srv)), None, "ibm_server_create")
     return srv
 
 
-def _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol=0.0):
+def _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol=0.0, mrt=None):
     d = LatticeDesc()
     d.nx, d.ny, d.tau, d.rho0 = int(nx), int(ny), float(tau), float(rho0)
     d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
@@ -355,6 +360,10 @@ def _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol
         d.wall_u[k][0], d.wall_u[k][1] = float(wu[2 * k]), float(wu[2 * k + 1])
     d.inlet_u[0], d.inlet_u[1] = float(inlet_u[0]), float(inlet_u[1])
     d.n_corr, d.corr_tol, d.delta_points = int(n_corr), float(corr_tol), 4
+    if mrt is not None:
+        d.collision = COLL_MRT
+        for k in range(3):
+            d.mrt_s[k] = float(mrt[k])
     return d
 
 
@@ -374,7 +383,7 @@ def ibm_server_submit(srv, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BO
     """Submit a workloads.Case for nsteps time steps; returns its id."""
     c = CaseDesc()
     c.lattice = _lattice_desc(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u,
-                              case.inlet_u, case.n_corr)
+                              case.inlet_u, case.n_corr, mrt=case.mrt)
     nb = len(case.bodies)
     bodies = (BodyDesc * max(nb, 1))(*[_body_desc(b) for b in case.bodies])
     nmark = (ctypes.c_int * max(nb, 1))(*[b.xy.shape[0] for b in case.bodies])
@@ -432,9 +441,10 @@ def ibm_server_last_error(srv=None) -> str:
 class Server:
     """Owning wrapper of an ibm_server (context manager)."""
 
-    def __init__(self, device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=100,
-                 ib_cta_budget=0):
-        self.s = ibm_server_create(device, max_device_bytes, max_active, steps_per_launch, ib_cta_budget)
+    def __init__(self, device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=32,
+                 ib_cta_budget=0, ib_markers_per_cta=0):
+        self.s = ibm_server_create(device, max_device_bytes, max_active, steps_per_launch, ib_cta_budget,
+                                   ib_markers_per_cta)
         self._shapes = {}
 
     def submit(self, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BODIES | OUT_RESIDUAL) -> int:
@@ -486,7 +496,8 @@ class Lattice:
     stream and PyTorch's caching allocator when PyTorch CUDA is present."""
 
     def __init__(self, nx, ny, tau, rho0=1.0, prec="fp32", bc=(PERIODIC,) * 4, wall_u=None,
-                 inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, device=0, torch_stream=True):
+                 inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, device=0, torch_stream=True,
+                 mrt=None):
         self.nx, self.ny, self.n_corr = int(nx), int(ny), int(n_corr)
         self.prec = prec
         self._stream = None
@@ -501,10 +512,11 @@ class Lattice:
             except ImportError:
                 pass
         self.h = ibm_create_lattice(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr,
-                                    corr_tol, stream_ptr, device)
+                                    corr_tol, stream_ptr, device, mrt)
 
     @classmethod
     def from_case(cls, case, prec="fp32", **kw):
+        kw.setdefault("mrt", case.mrt)
         lat = cls(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u, case.inlet_u,
                   case.n_corr, **kw)
         for b in case.bodies:
@@ -559,6 +571,10 @@ class Lattice:
 
     def kernel_times(self):
         return ibm_kernel_times(self.h)
+
+    def set_ib_ctas(self, n: int) -> None:
+        """CTAs of the correction-loop kernel (0: the default choice)."""
+        ibm_set_option(self.h, IBM_OPT_IB_CTAS, n)
 
     def counters(self):
         return ibm_get_counters(self.h)

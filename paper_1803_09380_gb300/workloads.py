@@ -60,6 +60,7 @@ class Case:
     inlet_u: tuple = (0.0, 0.0)
     n_corr: int = 10
     bodies: list = field(default_factory=list)
+    mrt: tuple | None = None  # None: BGK; else MRT rates (s_e, s_eps, s_q), Eq. 6
     meta: dict = field(default_factory=dict)
 
     @property

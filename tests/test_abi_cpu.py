@@ -30,7 +30,17 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert "ibm_step" in syms and "ibm_create_lattice" in syms
     for name in syms:
         assert hasattr(lib, name), f"{name} declared in ibm.h but not exported"
-    assert lib.ibm_abi_version() == 1
+    hdr = open(os.path.join(ROOT, "include", "ibm.h")).read()
+    assert lib.ibm_abi_version() == int(re.search(r"#define IBM_ABI_VERSION (\d+)", hdr).group(1))
+
+
+def test_descriptor_layout_matches_the_header():
+    """The ctypes mirror of ibm_lattice_desc ends with the collision fields
+    at the offsets a C compiler gives them (natural alignment)."""
+    d = ibm.LatticeDesc
+    assert d.collision.offset == d.device.offset + 4
+    assert d.mrt_s.offset % 8 == 0 and d.mrt_s.offset >= d.collision.offset + 4
+    assert ctypes.sizeof(d) == d.mrt_s.offset + 24
 
 
 def test_binding_covers_every_declared_symbol():
