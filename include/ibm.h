@@ -91,7 +91,10 @@ typedef struct {
   int n_corr;                 /* correction iterations N per step (paper: about 10) */
   double corr_tol;            /* 0: always N iterations; > 0: report
                                  IBM_WARN_NOT_CONVERGED when r^N > corr_tol */
-  int delta_points;           /* 4 (Eq. 15c); other kernels are not built */
+  int delta_points;           /* delta function of Eq. 15: 2 (15a), 3 (15b) or
+                                 4 (15c, the paper's choice); 0 means 4.  A
+                                 marker's 4 x 4 node window must stay inside
+                                 a non-periodic domain for every choice */
   void *cuda_stream;          /* cudaStream_t to enqueue on; NULL: the library
                                  creates its own stream, which synchronises
                                  with the legacy default stream */
@@ -148,7 +151,7 @@ enum {
 /* Creates a lattice in the rest equilibrium f_i = w_i rho0 (Eq. 3 with
  * u = 0) on desc->device.  Returns IBM_ERR_INVALID for nx or ny < 4, tau
  * <= 0.5 or not finite, an unpaired periodic side, an inlet/outlet on an
- * unsupported side, n_corr < 0 or delta_points != 4; IBM_ERR_NOMEM or
+ * unsupported side, n_corr < 0 or delta_points not 0, 2, 3, 4; IBM_ERR_NOMEM or
  * IBM_ERR_CUDA when device set-up fails.  *out is NULL on failure. */
 ibm_status ibm_create_lattice(const ibm_lattice_desc *desc, ibm_handle *out);
 

@@ -10,6 +10,9 @@ module.  It shares no code with the CUDA library: the arithmetic lives in
 Parity status of the functions (what pins each one is in ``tests/``):
   delta4, feq, moments            pinned by closed forms (partition of unity,
                                   sum of squares 3/8, equilibrium moments)
+  delta2, delta3 (Eq. 15a, b)     pinned by partition of unity, zero first
+                                  moment, sum of squares (1/2 for delta3) and
+                                  the straight-line contraction 1 - sum d^2
   IB correction loop              pinned by the straight-line 5/8 contraction
                                   and the isolated-marker 1 - 9/64 contraction
   collide + stream (periodic)     pinned by the shear-wave decay rate and
@@ -72,6 +75,10 @@ def _load():
         vp = ctypes.c_void_p
         lib.ora_delta4.restype = ctypes.c_double
         lib.ora_delta4.argtypes = [ctypes.c_double]
+        for name in ("ora_delta2", "ora_delta3"):
+            getattr(lib, name).restype = ctypes.c_double
+            getattr(lib, name).argtypes = [ctypes.c_double]
+        lib.ora_set_delta.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.ora_feq.argtypes = [ctypes.c_double] * 3 + [_D]
         lib.ora_moments.argtypes = [_D, _D, _D, _D]
         lib.ora_create.restype = vp
@@ -107,6 +114,16 @@ def _dp(a: np.ndarray):
 def delta4(r: float) -> float:
     """Eq. 15c, 4-point cosine delta function."""
     return _load().ora_delta4(float(r))
+
+
+def delta2(r: float) -> float:
+    """Eq. 15a: the 2-point delta function."""
+    return _load().ora_delta2(float(r))
+
+
+def delta3(r: float) -> float:
+    """Eq. 15b: the 3-point delta function."""
+    return _load().ora_delta3(float(r))
 
 
 def feq(rho: float, ux: float, uy: float) -> np.ndarray:
@@ -153,7 +170,7 @@ class Lattice:
     """
 
     def __init__(self, nx, ny, tau, rho0=1.0, bc=(0, 0, 0, 0), wall_u=None,
-                 inlet_u=(0.0, 0.0), n_corr=10, mrt=None):
+                 inlet_u=(0.0, 0.0), n_corr=10, mrt=None, delta_points=4):
         self._lib = _load()
         self.nx, self.ny, self.n_corr = int(nx), int(ny), int(n_corr)
         bc_a = (ctypes.c_int * 4)(*[int(b) for b in bc])
@@ -165,6 +182,9 @@ class Lattice:
             raise MemoryError("oracle lattice allocation failed")
         if mrt is not None:
             self._lib.ora_set_mrt(self._h, *[float(v) for v in mrt])
+        if delta_points not in (2, 3, 4):
+            raise ValueError("delta_points must be 2, 3 or 4 (Eq. 15a-c)")
+        self._lib.ora_set_delta(self._h, int(delta_points))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -79,6 +79,7 @@ typedef struct {
   double inlet_u[2];
   int n_corr;
   int mrt;                  /* 0: BGK, 1: MRT (Eqs. 2, 5, 6) */
+  int delta_points;         /* 2, 3 or 4: the delta function of Eq. 15a-c */
   double s_rate[ORA_Q];     /* diagonal of S in Eq. 6 */
   double *f;                /* [9][ny][nx], post-stream state */
   double *g;                /* streaming scratch */
@@ -101,6 +102,20 @@ double ora_delta4(double r) {
   double a = fabs(r);
   if (a >= 2.0) return 0.0;
   return 0.25 * (1.0 + cos(M_PI * a / 2.0));
+}
+
+/* Eq. 15a: 2-point (linear hat) delta function, zero for |r| >= 1. */
+double ora_delta2(double r) {
+  double a = fabs(r);
+  return a >= 1.0 ? 0.0 : 1.0 - a;
+}
+
+/* Eq. 15b: 3-point delta function, zero for |r| >= 1.5. */
+double ora_delta3(double r) {
+  double a = fabs(r);
+  if (a < 0.5) return (1.0 + sqrt(1.0 - 3.0 * a * a)) / 3.0;
+  if (a < 1.5) return (5.0 - 3.0 * a - sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a))) / 6.0;
+  return 0.0;
 }
 
 /* Eq. 3 with c_s^2 = 1/3. */
@@ -187,6 +202,7 @@ ora_lattice *ora_create(int nx, int ny, double tau, double rho0, const int *bc,
   L->inlet_u[0] = inlet_u ? inlet_u[0] : 0.0;
   L->inlet_u[1] = inlet_u ? inlet_u[1] : 0.0;
   L->n_corr = n_corr;
+  L->delta_points = 4;
   size_t n = (size_t)nx * ny;
   L->f = (double *)malloc(sizeof(double) * ORA_Q * n);
   L->g = (double *)malloc(sizeof(double) * ORA_Q * n);
@@ -218,6 +234,18 @@ void ora_set_mrt(ora_lattice *L, double s_e, double s_eps, double s_q) {
   double s[ORA_Q] = {sn, s_e, s_eps, sn, s_q, sn, s_q, sn, sn};
   L->mrt = 1;
   for (int k = 0; k < ORA_Q; ++k) L->s_rate[k] = s[k];
+}
+
+/* Choose the delta function of Eq. 15 (2, 3 or 4 points; 4 by default).
+ * Every support lies inside the 4 x 4 node window floor(X)-1 .. floor(X)+2,
+ * so interpolation and spreading keep that window; nodes outside the
+ * chosen support get weight zero. */
+void ora_set_delta(ora_lattice *L, int points) { L->delta_points = points; }
+
+static double delta_of(const ora_lattice *L, double r) {
+  if (L->delta_points == 2) return ora_delta2(r);
+  if (L->delta_points == 3) return ora_delta3(r);
+  return ora_delta4(r);
 }
 
 void ora_destroy(ora_lattice *L) {
@@ -303,11 +331,11 @@ static void interpolate_feq(const ora_lattice *L, int l, double *fs) {
   for (int b = 0; b < 4; ++b) {
     int y = axis_node(by + b, L->ny, py);
     if (y < 0) continue;
-    double wy = ora_delta4(L->Y[l] - (double)(by + b));
+    double wy = delta_of(L, L->Y[l] - (double)(by + b));
     for (int a = 0; a < 4; ++a) {
       int x = axis_node(bx + a, L->nx, px);
       if (x < 0) continue;
-      double wx = ora_delta4(L->X[l] - (double)(bx + a));
+      double wx = delta_of(L, L->X[l] - (double)(bx + a));
       double p[ORA_Q], rho, jx, jy, feq[ORA_Q];
       node_pops(L, L->f, x, y, p);
       ora_moments(p, &rho, &jx, &jy);
@@ -355,11 +383,11 @@ static double ib_iteration(ora_lattice *L, double *dfm) {
     for (int b = 0; b < 4; ++b) {
       int y = axis_node(by + b, L->ny, py);
       if (y < 0) continue;
-      double wy = ora_delta4(L->Y[l] - (double)(by + b));
+      double wy = delta_of(L, L->Y[l] - (double)(by + b));
       for (int a = 0; a < 4; ++a) {
         int x = axis_node(bx + a, L->nx, px);
         if (x < 0) continue;
-        double wx = ora_delta4(L->X[l] - (double)(bx + a));
+        double wx = delta_of(L, L->X[l] - (double)(bx + a));
         double W = wx * wy * L->ds[l];
         for (int i = 0; i < ORA_Q; ++i)
           L->df[idx(L, i, x, y)] += W * dfm[(size_t)l * ORA_Q + i];

@@ -340,8 +340,9 @@ ibm_status ibm::create_lattice(const ibm_lattice_desc* desc, ibm_handle* out, cu
     return fail(nullptr, IBM_ERR_INVALID, "inlet velocity not finite");
   if (d.n_corr < 0 || d.n_corr > 1000) return fail(nullptr, IBM_ERR_INVALID, "n_corr must be in [0, 1000]");
   if (!is_finite(d.corr_tol) || d.corr_tol < 0) return fail(nullptr, IBM_ERR_INVALID, "corr_tol must be >= 0");
-  if (d.delta_points != 4 && d.delta_points != 0)
-    return fail(nullptr, IBM_ERR_INVALID, "only the 4-point delta function (Eq. 15c) is built");
+  if (d.delta_points == 0) d.delta_points = 4;
+  if (d.delta_points < 2 || d.delta_points > 4)
+    return fail(nullptr, IBM_ERR_INVALID, "delta_points must be 2, 3 or 4 (Eq. 15a-c)");
 
   ibm_ctx* h = nullptr;
   try {
@@ -354,7 +355,6 @@ ibm_status ibm::create_lattice(const ibm_lattice_desc* desc, ibm_handle* out, cu
   Ctx& c = *h;
   c.pool = pool;
   c.desc = d;
-  c.desc.delta_points = 4;
   c.device = d.device;
   c.prec = d.prec;
   c.s_bytes = d.prec == IBM_FP64 ? 8 : (d.prec == IBM_FP32 ? 4 : 2);

@@ -33,6 +33,20 @@ __device__ __forceinline__ double delta4(double r) {
   return a >= 2.0 ? 0.0 : 0.25 * (1.0 + cospi(0.5 * a));
 }
 
+// Eq. 15a (2 points, the linear hat) and Eq. 15b (3 points).  Both supports
+// lie inside the 4 x 4 window floor(X)-1 .. floor(X)+2 that the band uses, so
+// the other kernels only change the weights (some become zero).
+__device__ __forceinline__ double delta_w(int points, double r) {
+  const double a = fabs(r);
+  if (points == 2) return a >= 1.0 ? 0.0 : 1.0 - a;
+  if (points == 3) {
+    if (a < 0.5) return (1.0 + sqrt(1.0 - 3.0 * a * a)) / 3.0;
+    if (a < 1.5) return (5.0 - 3.0 * a - sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a))) / 6.0;
+    return 0.0;
+  }
+  return delta4(r);
+}
+
 __device__ __forceinline__ int wrap_axis(int c, int n, bool periodic) {
   if (periodic) { c %= n; return c < 0 ? c + n : c; }
   return (c < 0 || c >= n) ? -1 : c;
@@ -70,7 +84,7 @@ __global__ void k_band_clear(Geom g, const int* __restrict__ ctr, const int* __r
 template <class R>
 __global__ void k_band_claim(Geom g, int M, const double* __restrict__ X, const double* __restrict__ Y,
                              R* __restrict__ W, int* __restrict__ node_of, int* __restrict__ node2band,
-                             int* __restrict__ claim) {
+                             int* __restrict__ claim, int points) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= M * kStencil) return;
   const int l = t / kStencil, s = t % kStencil;
@@ -82,7 +96,7 @@ __global__ void k_band_claim(Geom g, int M, const double* __restrict__ X, const 
   double w = 0.0;
   if (x >= 0 && y >= 0) {
     n = y * g.nx + x;
-    w = delta4(Xl - (double)bx) * delta4(Yl - (double)by);
+    w = delta_w(points, Xl - (double)bx) * delta_w(points, Yl - (double)by);
   }
   W[t] = (R)w;
   node_of[t] = n;
@@ -744,7 +758,7 @@ static void band_build_t(const Ctx& h, cudaStream_t s) {
                                                         h.dsegflag, h.nseg_x, h.bcap);
   cudaMemsetAsync(h.dctr, 0, 2 * sizeof(int), s);   // band nodes, band segments
   k_band_claim<R><<<blocks_for(T, 256), 256, 0, s>>>(h.geom, h.nm, h.dX, h.dY, (R*)h.dW, h.dnode_of,
-                                                      h.dnode2band, h.dclaim);
+                                                      h.dnode2band, h.dclaim, h.desc.delta_points);
   k_band_alloc<<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, h.dclaim, h.dnode2band, h.dbnode,
                                                   h.dbcnt, h.dctr, h.bcap);
   k_band_fill<R><<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, (const R*)h.dW, h.dds, h.dnode2band,

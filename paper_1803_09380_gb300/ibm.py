@@ -210,12 +210,12 @@ def use_torch_allocator() -> bool:
 
 def ibm_create_lattice(nx, ny, tau, rho0=1.0, prec="fp32", bc=(PERIODIC,) * 4, wall_u=None,
                        inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, stream=None, device=0,
-                       mrt=None):
+                       mrt=None, delta_points=4):
     """Create a lattice in the rest equilibrium; returns an opaque handle.
     ``mrt``: None for BGK, else the rates (s_e, s_eps, s_q) of Eq. 6 (a 0
     entry takes the value of section 3)."""
     lib = load()
-    d = _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol, mrt)
+    d = _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol, mrt, delta_points)
     d.cuda_stream = stream
     d.device = int(device)
     h = ctypes.c_void_p()
@@ -349,7 +349,8 @@ def ibm_server_create(device=0, max_device_bytes=0.0, max_active=16, steps_per_l
     return srv
 
 
-def _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol=0.0, mrt=None):
+def _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol=0.0, mrt=None,
+                  delta_points=4):
     d = LatticeDesc()
     d.nx, d.ny, d.tau, d.rho0 = int(nx), int(ny), float(tau), float(rho0)
     d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
@@ -359,7 +360,7 @@ def _lattice_desc(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr, corr_tol
     for k in range(4):
         d.wall_u[k][0], d.wall_u[k][1] = float(wu[2 * k]), float(wu[2 * k + 1])
     d.inlet_u[0], d.inlet_u[1] = float(inlet_u[0]), float(inlet_u[1])
-    d.n_corr, d.corr_tol, d.delta_points = int(n_corr), float(corr_tol), 4
+    d.n_corr, d.corr_tol, d.delta_points = int(n_corr), float(corr_tol), int(delta_points)
     if mrt is not None:
         d.collision = COLL_MRT
         for k in range(3):
@@ -383,7 +384,7 @@ def ibm_server_submit(srv, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BO
     """Submit a workloads.Case for nsteps time steps; returns its id."""
     c = CaseDesc()
     c.lattice = _lattice_desc(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u,
-                              case.inlet_u, case.n_corr, mrt=case.mrt)
+                              case.inlet_u, case.n_corr, mrt=case.mrt, delta_points=case.delta_points)
     nb = len(case.bodies)
     bodies = (BodyDesc * max(nb, 1))(*[_body_desc(b) for b in case.bodies])
     nmark = (ctypes.c_int * max(nb, 1))(*[b.xy.shape[0] for b in case.bodies])
@@ -497,7 +498,7 @@ class Lattice:
 
     def __init__(self, nx, ny, tau, rho0=1.0, prec="fp32", bc=(PERIODIC,) * 4, wall_u=None,
                  inlet_u=(0.0, 0.0), n_corr=10, corr_tol=0.0, device=0, torch_stream=True,
-                 mrt=None):
+                 mrt=None, delta_points=4):
         self.nx, self.ny, self.n_corr = int(nx), int(ny), int(n_corr)
         self.prec = prec
         self._stream = None
@@ -512,11 +513,12 @@ class Lattice:
             except ImportError:
                 pass
         self.h = ibm_create_lattice(nx, ny, tau, rho0, prec, bc, wall_u, inlet_u, n_corr,
-                                    corr_tol, stream_ptr, device, mrt)
+                                    corr_tol, stream_ptr, device, mrt, delta_points)
 
     @classmethod
     def from_case(cls, case, prec="fp32", **kw):
         kw.setdefault("mrt", case.mrt)
+        kw.setdefault("delta_points", case.delta_points)
         lat = cls(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u, case.inlet_u,
                   case.n_corr, **kw)
         for b in case.bodies:

@@ -61,6 +61,7 @@ class Case:
     n_corr: int = 10
     bodies: list = field(default_factory=list)
     mrt: tuple | None = None  # None: BGK; else MRT rates (s_e, s_eps, s_q), Eq. 6
+    delta_points: int = 4     # delta function of Eq. 15: 2, 3 or 4 points
     meta: dict = field(default_factory=dict)
 
     @property

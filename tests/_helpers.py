@@ -10,7 +10,8 @@ W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 
 def oracle_lattice(case, n_corr=None):
     L = oracle.Lattice(case.nx, case.ny, case.tau, case.rho0, case.bc, case.wall_u,
-                       case.inlet_u, case.n_corr if n_corr is None else n_corr, mrt=case.mrt)
+                       case.inlet_u, case.n_corr if n_corr is None else n_corr, mrt=case.mrt,
+                       delta_points=case.delta_points)
     for b in case.bodies:
         L.add_body(b.xy, b.ds, **b.as_kwargs())
     return L
@@ -18,7 +19,8 @@ def oracle_lattice(case, n_corr=None):
 
 def gpu_lattice(case, prec, n_corr=None):
     lat = ibm.Lattice(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u,
-                      case.inlet_u, case.n_corr if n_corr is None else n_corr, mrt=case.mrt)
+                      case.inlet_u, case.n_corr if n_corr is None else n_corr, mrt=case.mrt,
+                      delta_points=case.delta_points)
     for b in case.bodies:
         lat.add_markers(b.xy, b.ds, **b.as_kwargs())
     return lat
