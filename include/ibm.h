@@ -200,6 +200,17 @@ ibm_status ibm_get_sizes(ibm_handle h, long long *nodes, int *markers, int *bodi
  * Either pointer may be NULL. */
 ibm_status ibm_get_counters(ibm_handle h, long long *kernel_launches, long long *steps);
 
+/* Prescribes the velocity U_l of Eq. 24 marker by marker: uv holds (u_x, u_y)
+ * interleaved for all n markers of h (n must equal the marker count), in
+ * the order they were added.  It applies to markers of FIXED bodies from
+ * the next step on and stays until the next call -- a time-dependent
+ * boundary (e.g. the Taylor-Green case of section 3.1.1, Eq. 30) calls it
+ * before every step.  Markers of moving bodies keep taking their velocity
+ * from the body motion; adding markers resets every marker to its body's
+ * u + omega x (X - xc).  The array is copied before the call returns.
+ * Errors: IBM_ERR_INVALID for NULL, a wrong n or a non-finite value. */
+ibm_status ibm_set_marker_velocities(ibm_handle h, const double *uv, int n);
+
 /* Tuning options for ibm_set_option. */
 enum {
   IBM_OPT_IB_CTAS = 1   /* CTAs of the correction kernel: 0 (default) = one CTA for up to 512

@@ -79,6 +79,8 @@ def _load():
             getattr(lib, name).restype = ctypes.c_double
             getattr(lib, name).argtypes = [ctypes.c_double]
         lib.ora_set_delta.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.ora_set_marker_velocities.restype = ctypes.c_int
+        lib.ora_set_marker_velocities.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
         lib.ora_feq.argtypes = [ctypes.c_double] * 3 + [_D]
         lib.ora_moments.argtypes = [_D, _D, _D, _D]
         lib.ora_create.restype = vp
@@ -204,6 +206,13 @@ class Lattice:
                        volume, inertia, radius, gravity[0], gravity[1]], dtype=np.float64)
         return self._lib.ora_add_body(self._h, int(kind), _dp(bd), _dp(xy), _dp(ds),
                                       xy.shape[0])
+
+    def set_marker_velocities(self, uv):
+        """Prescribed U_l of every marker of a fixed body, (M, 2) array,
+        from the next step on."""
+        uv = np.ascontiguousarray(uv, dtype=np.float64).reshape(-1, 2)
+        if self._lib.ora_set_marker_velocities(self._h, _dp(uv), uv.shape[0]) != 0:
+            raise ValueError("one velocity pair per marker is required")
 
     # ---- stepping
     def step(self, n=1):

@@ -87,6 +87,7 @@ typedef struct {
   double *rho, *ux, *uy;    /* moments of the last corrected state */
   int nm, mcap;
   double *X, *Y, *ds, *dX, *dY; /* marker positions, arc lengths, offsets */
+  double *Uset;             /* prescribed marker velocities [2 nm], or NULL */
   int *mbody;
   int nb, bcap;
   ora_body *bodies;
@@ -253,7 +254,7 @@ void ora_destroy(ora_lattice *L) {
   free(L->f); free(L->g); free(L->df);
   free(L->rho); free(L->ux); free(L->uy); free(L->resid);
   free(L->X); free(L->Y); free(L->ds); free(L->dX); free(L->dY);
-  free(L->mbody); free(L->bodies);
+  free(L->mbody); free(L->bodies); free(L->Uset);
   free(L);
 }
 
@@ -261,6 +262,8 @@ void ora_destroy(ora_lattice *L) {
  * radius, gravity[2] -- packed as 14 doubles after the kind. */
 int ora_add_body(ora_lattice *L, int kind, const double *bd, const double *xy,
                  const double *ds, int n) {
+  free(L->Uset);            /* prescribed velocities are reset by new markers */
+  L->Uset = NULL;
   if (L->nm + n > L->mcap) {
     int cap = (L->nm + n) * 2;
     L->X = (double *)realloc(L->X, sizeof(double) * cap);
@@ -308,8 +311,25 @@ int ora_add_body(ora_lattice *L, int kind, const double *bd, const double *xy,
 /* Velocity of marker l: rigid motion of its body, U + omega x (X - xc). */
 static void marker_velocity(const ora_lattice *L, int l, double *U) {
   const ora_body *B = &L->bodies[L->mbody[l]];
+  if (L->Uset && B->kind == ORA_BODY_FIXED) {
+    U[0] = L->Uset[2 * l];
+    U[1] = L->Uset[2 * l + 1];
+    return;
+  }
   U[0] = B->u[0] - B->omega * (L->Y[l] - B->xc[1]);
   U[1] = B->u[1] + B->omega * (L->X[l] - B->xc[0]);
+}
+
+/* Prescribe the velocity U_l of Eq. 24 marker by marker (interleaved u_x,
+ * u_y for all markers) for markers of fixed bodies, from the next step on;
+ * a time-dependent boundary sets it before every step. */
+int ora_set_marker_velocities(ora_lattice *L, const double *uv, int n) {
+  if (n != L->nm) return -1;
+  double *u = (double *)realloc(L->Uset, sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+  if (!u) return -1;
+  L->Uset = u;
+  for (int k = 0; k < 2 * n; ++k) L->Uset[k] = uv[k];
+  return 0;
 }
 
 /* Lattice index of stencil coordinate c along an axis of length n, or -1

@@ -605,6 +605,53 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
   }
 }
 
+ibm_status ibm_set_marker_velocities(ibm_handle h, const double* uv, int n) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (!uv || n != h->nm) return fail(h, IBM_ERR_INVALID, "uv must hold one (u_x, u_y) pair per marker");
+  for (int k = 0; k < 2 * n; ++k)
+    if (!is_finite(uv[k])) return fail(h, IBM_ERR_INVALID, "marker velocity not finite");
+  if (n == 0) return IBM_OK;
+  try {
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(h, IBM_ERR_CUDA, "cannot select the CUDA device");
+    Ctx& c = *h;
+    const int R = c.r_bytes;
+    std::vector<char> ux((size_t)R * n), uy((size_t)R * n);
+    for (int l = 0; l < n; ++l) {
+      if (c.hbodies[c.hmbody[l]].kind != IBM_BODY_FIXED) continue;
+      c.hUx[l] = uv[2 * l];
+      c.hUy[l] = uv[2 * l + 1];
+    }
+    for (int l = 0; l < n; ++l) {
+      if (R == 8) { ((double*)ux.data())[l] = c.hUx[l]; ((double*)uy.data())[l] = c.hUy[l]; }
+      else { ((float*)ux.data())[l] = (float)c.hUx[l]; ((float*)uy.data())[l] = (float)c.hUy[l]; }
+    }
+    // Pageable sources are staged before cudaMemcpyAsync returns, so the
+    // temporaries may go; the copies are ordered before the next step.
+    if (c.any_moving) {
+      // moving markers' device velocities are newer than hUx: copy only
+      // the fixed bodies' marker ranges
+      int l = 0;
+      while (l < n) {
+        if (c.hbodies[c.hmbody[l]].kind != IBM_BODY_FIXED) { ++l; continue; }
+        int e = l;
+        while (e < n && c.hmbody[e] == c.hmbody[l]) ++e;
+        IBM_CK(h, cudaMemcpyAsync((char*)c.dUx + (size_t)R * l, ux.data() + (size_t)R * l, (size_t)R * (e - l),
+                                  cudaMemcpyHostToDevice, c.stream));
+        IBM_CK(h, cudaMemcpyAsync((char*)c.dUy + (size_t)R * l, uy.data() + (size_t)R * l, (size_t)R * (e - l),
+                                  cudaMemcpyHostToDevice, c.stream));
+        l = e;
+      }
+    } else {
+      IBM_CK(h, cudaMemcpyAsync(c.dUx, ux.data(), (size_t)R * n, cudaMemcpyHostToDevice, c.stream));
+      IBM_CK(h, cudaMemcpyAsync(c.dUy, uy.data(), (size_t)R * n, cudaMemcpyHostToDevice, c.stream));
+    }
+    return IBM_OK;
+  } catch (...) {
+    return fail(h, IBM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
 ibm_status ibm_sync(ibm_handle h) {
   if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
   DeviceGuard guard(h->device);

@@ -211,7 +211,8 @@ __device__ __forceinline__ S shfl_down1(S v) { return __shfl_down_sync(0xfffffff
 template <int P, bool MACRO, bool MRT, int VEC>
 __device__ __forceinline__ void collide_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                             typename Prec<P>::R (&p)[9][VEC],
-                                            typename Prec<P>::R* __restrict__ mac, int x0, int y) {
+                                            typename Prec<P>::R* __restrict__ mac, int x0, int y,
+                                            bool active = true) {
   typedef typename Prec<P>::R R;
 #pragma unroll
   for (int k = 0; k < VEC; ++k) {
@@ -225,7 +226,8 @@ __device__ __forceinline__ void collide_vec(const Geom& g, const StepConsts<type
     } else {
       collide<R, MRT>(q, qs, rho, jx, jy, c);
     }
-    if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x0 + k, rho, jx, jy);
+    if (MACRO && active)
+      write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x0 + k, rho, jx, jy);
 #pragma unroll
     for (int i = 0; i < 9; ++i) p[i][k] = qs[i];
   }
@@ -259,48 +261,60 @@ __device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typenam
 }
 
 // Odd step for one warp span of 32 * VEC consecutive nodes of row y that
-// holds no boundary node (every lane active; periodic wrap only across the
-// row ends).  Each lane owns nodes x0 .. x0+VEC-1.  Loads and stores are
-// aligned vectors; the one-element shift of the directions with an
-// x component is done with warp shuffles.  Elements that cross to the
-// neighbouring span are read or written with scalar accesses by the thread
-// whose node owns the slot (lane 0 and lane 31), so spans never write each
-// other's slots.
+// holds no boundary node (periodic wrap only across the row ends).  Each
+// lane owns nodes x0 .. x0+VEC-1.  Loads and stores are aligned vectors; the
+// one-element shift of the directions with an x component is done with warp
+// shuffles.  A lane with `skip` set (its nodes lie in a band segment, which
+// another kernel streams) loads and stores nothing.  Elements that cross to
+// the neighbouring span or to a skipped lane are read or written with
+// scalar accesses by the thread whose node owns the slot (the lanes at the
+// ends of each run of active lanes), so no slot of another node is written.
 template <int P, bool MACRO, bool MRT>
 __device__ __forceinline__ void odd_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                         typename Prec<P>::S* __restrict__ A,
-                                        typename Prec<P>::R* __restrict__ mac, int x0, int y, int lane) {
+                                        typename Prec<P>::R* __restrict__ mac, int x0, int y, int lane,
+                                        bool skip) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
   constexpr int VEC = VecTraits<P>::VEC;
   const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;              // left of the lane's nodes
   const int xr = x0 + VEC == g.nx ? 0 : x0 + VEC;           // right of the lane's nodes
   const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+  const bool skip_l = __shfl_up_sync(0xffffffffu, skip, 1);
+  const bool skip_r = __shfl_down_sync(0xffffffffu, skip, 1);
+  const bool lo = lane == 0 || skip_l;                      // left end of an active run
+  const bool hi = lane == 31 || skip_r;                     // right end of an active run
   R p[9][VEC];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int sy = cy(i) > 0 ? ym : (cy(i) < 0 ? yp : y);
     const int sl = opp(i);
     const S* row = A + sl * g.plane + (long long)sy * g.nxp;
-    const SVec<S, VEC> v = vload<S, VEC>(row + x0);
+    SVec<S, VEC> v;
+    if (!skip) {
+      v = vload<S, VEC>(row + x0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) v.v[k] = S(0);
+    }
     if (cx(i) == 0) {
 #pragma unroll
       for (int k = 0; k < VEC; ++k) p[i][k] = Prec<P>::ld(v.v[k], sl);
     } else if (cx(i) > 0) {                                  // f_i(x) sits at x - 1
       S left = shfl_up1<S>(v.v[VEC - 1]);
-      if (lane == 0) left = row[xl];
+      if (lo && !skip) left = row[xl];
       p[i][0] = Prec<P>::ld(left, sl);
 #pragma unroll
       for (int k = 1; k < VEC; ++k) p[i][k] = Prec<P>::ld(v.v[k - 1], sl);
     } else {                                                 // f_i(x) sits at x + 1
       S right = shfl_down1<S>(v.v[0]);
-      if (lane == 31) right = row[xr];
+      if (hi && !skip) right = row[xr];
 #pragma unroll
       for (int k = 0; k < VEC - 1; ++k) p[i][k] = Prec<P>::ld(v.v[k + 1], sl);
       p[i][VEC - 1] = Prec<P>::ld(right, sl);
     }
   }
-  collide_vec<P, MACRO, MRT, VEC>(g, c, p, mac, x0, y);
+  collide_vec<P, MACRO, MRT, VEC>(g, c, p, mac, x0, y, !skip);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int ty = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
@@ -312,33 +326,37 @@ __device__ __forceinline__ void odd_vec(const Geom& g, const StepConsts<typename
       SVec<S, VEC> v;
 #pragma unroll
       for (int k = 0; k < VEC; ++k) v.v[k] = o[k];
-      vstore<S, VEC>(row + x0, v);
+      if (!skip) vstore<S, VEC>(row + x0, v);
     } else if (cx(i) > 0) {                                  // node x writes slot x + 1
       const S from_left = shfl_up1<S>(o[VEC - 1]);
-      if (lane == 0) {
+      if (!skip) {
+        if (lo) {
 #pragma unroll
-        for (int k = 0; k < VEC - 1; ++k) row[x0 + 1 + k] = o[k];
-      } else {
-        SVec<S, VEC> v;
-        v.v[0] = from_left;
+          for (int k = 0; k < VEC - 1; ++k) row[x0 + 1 + k] = o[k];
+        } else {
+          SVec<S, VEC> v;
+          v.v[0] = from_left;
 #pragma unroll
-        for (int k = 1; k < VEC; ++k) v.v[k] = o[k - 1];
-        vstore<S, VEC>(row + x0, v);
+          for (int k = 1; k < VEC; ++k) v.v[k] = o[k - 1];
+          vstore<S, VEC>(row + x0, v);
+        }
+        if (hi) row[xr] = o[VEC - 1];
       }
-      if (lane == 31) row[xr] = o[VEC - 1];
     } else {                                                 // node x writes slot x - 1
       const S from_right = shfl_down1<S>(o[0]);
-      if (lane == 31) {
+      if (!skip) {
+        if (hi) {
 #pragma unroll
-        for (int k = 1; k < VEC; ++k) row[x0 + k - 1] = o[k];
-      } else {
-        SVec<S, VEC> v;
+          for (int k = 1; k < VEC; ++k) row[x0 + k - 1] = o[k];
+        } else {
+          SVec<S, VEC> v;
 #pragma unroll
-        for (int k = 0; k < VEC - 1; ++k) v.v[k] = o[k + 1];
-        v.v[VEC - 1] = from_right;
-        vstore<S, VEC>(row + x0, v);
+          for (int k = 0; k < VEC - 1; ++k) v.v[k] = o[k + 1];
+          v.v[VEC - 1] = from_right;
+          vstore<S, VEC>(row + x0, v);
+        }
+        if (lo) row[xl] = o[0];
       }
-      if (lane == 0) row[xl] = o[0];
     }
   }
 }

@@ -31,8 +31,9 @@ namespace ibm {
 //   (the correction-loop kernel streams those segments after correcting
 //   them).
 // Even step: per lane, aligned vectors (ragged row ends node by node).  Odd
-// step: spans without boundary, ragged or band nodes take the vector path;
-// the others go node by node through the boundary-aware path.
+// step: spans without boundary or ragged nodes take the vector path (lanes
+// whose nodes lie in band segments sit out); the others go node by node
+// through the boundary-aware path.
 template <int P, int PAR, bool MACRO, int MODE, bool MRT>
 __global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
                                                         typename Prec<P>::S* __restrict__ A,
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typen
   const int x_special = closed_x ? (g.bc[1] == BC_OUTLET ? g.nx - 2 : g.nx - 1) : g.nx;
   const bool edge = (g.bc[2] != BC_PERIODIC && (y == 0 || y == g.ny - 1)) ||
                     (closed_x && xw == 0) || (xw + 32 * VEC > x_special) || (xw + 32 * VEC > g.nx);
-  if (edge || __any_sync(0xffffffffu, flagged)) {
+  if (edge) {
     for (int k = 0; k < VEC; ++k) {
       const int x = x0 + k;
       if (x >= g.nx) break;
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typen
     }
     return;
   }
-  odd_vec<P, MACRO, MRT>(g, c, A, mac, x0, y, lane);
+  if (__all_sync(0xffffffffu, flagged)) return;               // the whole span is band segments
+  odd_vec<P, MACRO, MRT>(g, c, A, mac, x0, y, lane, flagged);
 }
 
 // ------------------------------------------------------------------ fields

@@ -45,7 +45,7 @@ SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields
            "ibm_abi_version", "ibm_ib_correct_noalloc", "ibm_set_option",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_wait",
            "ibm_server_result", "ibm_server_release", "ibm_server_get_stats", "ibm_server_destroy",
-           "ibm_server_last_error")
+           "ibm_server_last_error", "ibm_set_marker_velocities")
 IBM_OPT_IB_CTAS = 1
 OUT_MACRO, OUT_BODIES, OUT_RESIDUAL = 1, 2, 4
 
@@ -144,6 +144,7 @@ def load(build_if_missing: bool = True):
         lib.ibm_abi_version.restype = ci
         lib.ibm_ib_correct_noalloc.argtypes = [ci, ci, ci, vp, ci, vp, vp, vp, ci, vp, vp, vp]
         lib.ibm_set_option.argtypes = [vp, ci, ctypes.c_longlong]
+        lib.ibm_set_marker_velocities.argtypes = [vp, _D, ci]
         lib.ibm_server_create.argtypes = [ctypes.POINTER(ServerDesc), ctypes.POINTER(vp)]
         lib.ibm_server_submit.argtypes = [vp, ctypes.POINTER(CaseDesc), ctypes.POINTER(ctypes.c_longlong)]
         lib.ibm_server_progress.argtypes = [vp, ctypes.POINTER(ci)]
@@ -327,6 +328,13 @@ def ibm_ib_correct_noalloc(nx, ny, prec, f_ptr, n_markers, xy_ptr, ds_ptr, uvel_
     _check(load().ibm_ib_correct_noalloc(int(nx), int(ny), p, f_ptr, int(n_markers), xy_ptr, ds_ptr,
                                          uvel_ptr, int(n_corr), resid_ptr, force_ptr, stream),
            None, "ibm_ib_correct_noalloc")
+
+
+def ibm_set_marker_velocities(h, uv) -> None:
+    """Prescribed velocity of every marker of a fixed body, (M, 2) array."""
+    uv = np.ascontiguousarray(uv, dtype=np.float64).reshape(-1, 2)
+    _check(load().ibm_set_marker_velocities(h, uv.ctypes.data_as(_D), uv.shape[0]), h,
+           "ibm_set_marker_velocities")
 
 
 def ibm_set_option(h, option: int, value: int) -> None:
@@ -573,6 +581,10 @@ class Lattice:
 
     def kernel_times(self):
         return ibm_kernel_times(self.h)
+
+    def set_marker_velocities(self, uv) -> None:
+        """Prescribed U_l of every marker of a fixed body from the next step on."""
+        ibm_set_marker_velocities(self.h, uv)
 
     def set_ib_ctas(self, n: int) -> None:
         """CTAs of the correction-loop kernel (0: the default choice)."""

@@ -120,6 +120,44 @@ def couette_analytic(case: Case, x: np.ndarray, y: np.ndarray):
     return ut * sx, ut * sy
 
 
+def taylor_green(L: int, re: float = 10.0, tau: float = 0.65, n_corr: int = 10,
+                 markers: int | None = None) -> Case:
+    """Taylor-Green vortices with an artificial cylinder (section 3.1.1): a
+    periodic 2L x 2L lattice whose node i sits at x = i + 1/2 - L (the
+    vortex field of Eq. 30 has period 2L), a cylinder of diameter L at the
+    centre whose markers follow Eq. 30, Re = u0 L / nu (10) and tau (0.65)
+    fixing u0.  Marker velocities change every step: see taylor_green_fields."""
+    nu = (tau - 0.5) / 3.0
+    u0 = re * nu / L
+    c = L - 0.5
+    xy, ds = ring(c, c, L / 2.0, count=markers)
+    body = Body(xy, ds, BODY_FIXED, xc=(c, c), radius=L / 2.0)
+    return Case(f"tgv{L}", 2 * L, 2 * L, tau, n_corr=n_corr, bodies=[body],
+                meta=dict(L=L, u0=u0, nu=nu, center=c, re=re))
+
+
+def taylor_green_fields(case: Case, x, y, t: float):
+    """Eq. 30 at lattice coordinates (x, y) and time t: (rho, u_x, u_y).
+    Readings of the garbled print: u_y = +u0 sin(kx) cos(ky) (the printed
+    sign gives a divergent field) and the density of the standard vortex
+    pressure, rho = rho0 - 3 u0^2/4 (cos 2kx + cos 2ky) e^{-4 nu k^2 t}
+    (p = c_s^2 rho), with k = pi / L and rho0 = 1."""
+    m = case.meta
+    k = math.pi / m["L"]
+    X = np.asarray(x, dtype=np.float64) - m["center"]
+    Y = np.asarray(y, dtype=np.float64) - m["center"]
+    d = math.exp(-2.0 * m["nu"] * k * k * t)
+    ux = -m["u0"] * np.cos(k * X) * np.sin(k * Y) * d
+    uy = m["u0"] * np.sin(k * X) * np.cos(k * Y) * d
+    rho = 1.0 - 0.75 * m["u0"] ** 2 * (np.cos(2 * k * X) + np.cos(2 * k * Y)) * d * d
+    return rho, ux, uy
+
+
+def taylor_green_steps(case: Case) -> int:
+    """Time steps to t* = t u0 / L = 1."""
+    return int(round(case.meta["L"] / case.meta["u0"]))
+
+
 def cylinder(nx: int = 1600, ny: int = 800, diameter: float = 40.0,
              center: tuple = (400.0, 400.0), u_in: float = 0.05,
              re: float = 20.0, markers: int = 126, n_corr: int = 10) -> Case:
