@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--ib-ctas", type=int, default=0,
                    help="CTAs of the correction kernel (0: the library's choice)")
+    p.add_argument("--ib-threads", type=int, default=0,
+                   help="threads per correction-kernel CTA (0: the library's choice)")
     p.add_argument("--serve-requests", type=int, default=64)
     p.add_argument("--serve-steps", type=int, default=500)
     p.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
@@ -244,6 +246,8 @@ def run_ours(args, rank, world, local_rank, dist):
     lat = ibm.Lattice.from_case(case, prec=args.prec, device=local_rank)
     if args.ib_ctas:
         lat.set_ib_ctas(args.ib_ctas)
+    if args.ib_threads:
+        lat.set_ib_threads(args.ib_threads)
     stream = lat._stream
     flags = ibm.STEP_TIME_KERNELS | ibm.STEP_NO_MACRO
 

@@ -213,9 +213,10 @@ ibm_status ibm_set_marker_velocities(ibm_handle h, const double *uv, int n);
 
 /* Tuning options for ibm_set_option. */
 enum {
-  IBM_OPT_IB_CTAS = 1   /* CTAs of the correction kernel: 0 (default) = one CTA for up to 512
+  IBM_OPT_IB_CTAS = 1,  /* CTAs of the correction kernel: 0 (default) = one CTA for up to 512
                            markers, one per SM above that; n > 0 = min(n, SMs).  Results do not
                            depend on it. */
+  IBM_OPT_IB_THREADS = 2 /* threads per correction-kernel CTA: 256 (default), 512 or 1024 */
 };
 
 /* Sets a tuning option of h (takes effect at the next step).  Concurrency

@@ -807,6 +807,17 @@ ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodi
 
 ibm_status ibm_set_option(ibm_handle h, int option, long long value) {
   if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (option == IBM_OPT_IB_THREADS) {
+    if (value != 256 && value != 512 && value != 1024)
+      return fail(h, IBM_ERR_INVALID, "IBM_OPT_IB_THREADS must be 256, 512 or 1024");
+    DeviceGuard guard(h->device);
+    if (ib_blocks_per_sm(h->prec, (int)value) < 1)
+      return fail(h, IBM_ERR_INVALID, "the correction kernel cannot be resident with that many threads");
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->ib_threads = (int)value;
+    destroy_graphs(*h);
+    return IBM_OK;
+  }
   if (option != IBM_OPT_IB_CTAS) return fail(h, IBM_ERR_INVALID, "unknown option");
   if (value < 0 || value > (1 << 20)) return fail(h, IBM_ERR_INVALID, "IBM_OPT_IB_CTAS out of range");
   h->ib_grid_opt = (int)value;

@@ -284,7 +284,7 @@ __device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr, 
   __syncthreads();
   if (threadIdx.x == 0 && dst) {
     R m = red[0];
-    for (int k = 1; k < kIbThreads / 32; ++k) m = nanmax(m, red[k]);
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = nanmax(m, red[k]);
     if (m > R(0) || m != m) AtomicBits<R>::max(dst, m);
   }
   if (gridDim.x == 1) {                           // one CTA: a block barrier suffices
@@ -323,11 +323,11 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
     b += __shfl_xor_sync(0xffffffffu, b, off);
     c += __shfl_xor_sync(0xffffffffu, c, off);
   }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { sh[w] = a; sh[8 + w] = b; sh[16 + w] = c; }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sh[w] = a; sh[32 + w] = b; sh[64 + w] = c; }
   __syncthreads();
-  a = sh[0]; b = sh[8]; c = sh[16];
-  for (int k = 1; k < kIbThreads / 32; ++k) { a += sh[k]; b += sh[8 + k]; c += sh[16 + k]; }
+  a = sh[0]; b = sh[32]; c = sh[64];
+  for (int k = 1; k < nw; ++k) { a += sh[k]; b += sh[32 + k]; c += sh[64 + k]; }
   __syncthreads();
 }
 
@@ -396,11 +396,11 @@ __device__ __forceinline__ void deviation(const Args& a, int l, const R* __restr
   djy = a.mq[4 * l + 2] - sy;
 }
 
-template <int P, int PAR>
-__global__ void __launch_bounds__(kIbThreads) k_ib_step(IbArgs<P> a) {
+template <int P, int PAR, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) {
   typedef typename Prec<P>::R R;
-  __shared__ R red[kIbThreads / 32];
-  __shared__ double sh[24];
+  __shared__ R red[NT / 32];
+  __shared__ double sh[96];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const int rtid = nth - 1 - tid;                  // band work starts from the other end
@@ -826,9 +826,20 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   a.fpart = h.dfpart;
   a.bar = h.dbar;
   cudaMemsetAsync(h.dresid, 0, sizeof(R) * (a.N + 1), s);
-  const dim3 grid(h.ib_grid), block(kIbThreads);
-  if (parity == 0) launch_prio(k_ib_step<P, 0>, grid, block, s, h.ib_prio, a);
-  else launch_prio(k_ib_step<P, 1>, grid, block, s, h.ib_prio, a);
+  const dim3 grid(h.ib_grid), block(h.ib_threads);
+  switch (h.ib_threads) {
+    case 512:
+      if (parity == 0) launch_prio(k_ib_step<P, 0, 512>, grid, block, s, h.ib_prio, a);
+      else launch_prio(k_ib_step<P, 1, 512>, grid, block, s, h.ib_prio, a);
+      break;
+    case 1024:
+      if (parity == 0) launch_prio(k_ib_step<P, 0, 1024>, grid, block, s, h.ib_prio, a);
+      else launch_prio(k_ib_step<P, 1, 1024>, grid, block, s, h.ib_prio, a);
+      break;
+    default:
+      if (parity == 0) launch_prio(k_ib_step<P, 0, kIbThreads>, grid, block, s, h.ib_prio, a);
+      else launch_prio(k_ib_step<P, 1, kIbThreads>, grid, block, s, h.ib_prio, a);
+  }
   // the band segments, once corrected
   if (h.band_collide) {
     const int need = (h.segcap * kSegW + 255) / 256;
@@ -851,19 +862,30 @@ void launch_ib_loop(const Ctx& h, int parity, bool macro, cudaStream_t s) {
 // Largest co-resident CTA count of the correction-loop kernel (1 per SM is
 // used; the kernel's grid barrier needs every CTA resident).
 template <int P>
-static int ib_blocks_per_sm_t() {
+static int ib_blocks_per_sm_t(int threads) {
   int n0 = 0, n1 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ib_step<P, 0>, kIbThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ib_step<P, 1>, kIbThreads, 0);
+  switch (threads) {
+    case 512:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ib_step<P, 0, 512>, 512, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ib_step<P, 1, 512>, 512, 0);
+      break;
+    case 1024:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ib_step<P, 0, 1024>, 1024, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ib_step<P, 1, 1024>, 1024, 0);
+      break;
+    default:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_ib_step<P, 0, kIbThreads>, kIbThreads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_ib_step<P, 1, kIbThreads>, kIbThreads, 0);
+  }
   return n0 < n1 ? n0 : n1;
 }
 
-int ib_blocks_per_sm(int prec) {
+int ib_blocks_per_sm(int prec, int threads) {
   switch (prec) {
-    case PREC_FP64: return ib_blocks_per_sm_t<PREC_FP64>();
-    case PREC_FP32: return ib_blocks_per_sm_t<PREC_FP32>();
-    case PREC_FP16_DEV: return ib_blocks_per_sm_t<PREC_FP16_DEV>();
-    default: return ib_blocks_per_sm_t<PREC_BF16_DEV>();
+    case PREC_FP64: return ib_blocks_per_sm_t<PREC_FP64>(threads);
+    case PREC_FP32: return ib_blocks_per_sm_t<PREC_FP32>(threads);
+    case PREC_FP16_DEV: return ib_blocks_per_sm_t<PREC_FP16_DEV>(threads);
+    default: return ib_blocks_per_sm_t<PREC_BF16_DEV>(threads);
   }
 }
 

@@ -111,6 +111,7 @@ struct Ctx {
   unsigned long long* dbar = nullptr;        // grid-barrier arrivals of the correction kernel
   int ib_grid = 0;                           // CTAs of the correction kernel
   int ib_grid_max = 0;                       // one per SM
+  int ib_threads = kIbThreads;               // threads per correction-loop CTA: 256, 512, 1024
   int ib_grid_opt = 0;                       // caller's choice (IBM_OPT_IB_CTAS), 0 = by size
   bool band_collide = true;                  // stream the band segments after the correction
   bool band_valid = false;
@@ -212,7 +213,7 @@ void launch_fields(const Ctx& h, int op, const double* dev_in, double* dev_out, 
 // ibm_ib.cu
 void launch_band_build(const Ctx& h, cudaStream_t s);
 void launch_ib_loop(const Ctx& h, int parity, bool macro, cudaStream_t s);
-int ib_blocks_per_sm(int prec);
+int ib_blocks_per_sm(int prec, int threads = kIbThreads);
 void launch_body_update(const Ctx& h, cudaStream_t s);
 
 }  // namespace ibm

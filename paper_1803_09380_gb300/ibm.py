@@ -46,7 +46,7 @@ SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_wait",
            "ibm_server_result", "ibm_server_release", "ibm_server_get_stats", "ibm_server_destroy",
            "ibm_server_last_error", "ibm_set_marker_velocities")
-IBM_OPT_IB_CTAS = 1
+IBM_OPT_IB_CTAS, IBM_OPT_IB_THREADS = 1, 2
 OUT_MACRO, OUT_BODIES, OUT_RESIDUAL = 1, 2, 4
 
 
@@ -589,6 +589,10 @@ class Lattice:
     def set_ib_ctas(self, n: int) -> None:
         """CTAs of the correction-loop kernel (0: the default choice)."""
         ibm_set_option(self.h, IBM_OPT_IB_CTAS, n)
+
+    def set_ib_threads(self, n: int) -> None:
+        """Threads per correction-loop CTA: 256, 512 or 1024."""
+        ibm_set_option(self.h, IBM_OPT_IB_THREADS, n)
 
     def counters(self):
         return ibm_get_counters(self.h)

@@ -118,13 +118,14 @@ def test_mrt_rates_are_validated():
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_correction_results_do_not_depend_on_cta_count(prec):
     """The correction kernel's sums use fixed chunks and trees, so any CTA
-    count (one CTA with a block barrier, or a grid barrier over many) gives
-    bitwise the same state, residuals and body forces."""
+    count (one CTA with a block barrier, or a grid barrier over many) and
+    any CTA size give bitwise the same state, residuals and body forces."""
     case = wl.couette(256)
     ref = None
-    for ctas in (0, 1, 3, 152):
+    for ctas, threads in ((0, 256), (1, 256), (3, 256), (152, 256), (2, 512), (19, 1024)):
         lat = gpu_lattice(case, prec)
         lat.set_ib_ctas(ctas)
+        lat.set_ib_threads(threads)
         lat.step(12)
         got = (lat.f, lat.resid, lat.bodies)
         if ref is None:
