@@ -214,8 +214,9 @@ ibm_status ibm_set_marker_velocities(ibm_handle h, const double *uv, int n);
 /* Tuning options for ibm_set_option. */
 enum {
   IBM_OPT_IB_CTAS = 1,  /* CTAs of the correction kernel: 0 (default) = one CTA for up to 512
-                           markers, one per SM above that; n > 0 = min(n, SMs).  Results do not
-                           depend on it. */
+                           markers, 3 per 4 SMs above that; n > 0 = min(n, SMs).  2..16 CTAs
+                           run as one thread-block cluster when the device can schedule it.
+                           Results do not depend on it. */
   IBM_OPT_IB_THREADS = 2 /* threads per correction-kernel CTA: 256 (default), 512 or 1024 */
 };
 

@@ -100,7 +100,9 @@ cudaError_t capture_steps(Ctx& c, int parity, int count, bool macro_last, cudaGr
     enqueue_step(c, parity ^ (j & 1), macro_last && j == count - 1, false);
   e = cudaStreamEndCapture(c.stream, &graph);
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(out, graph, 0);
+  // per-node priorities: the correction chain keeps its high priority inside
+  // the graph (by default a graph runs at the priority of its stream)
+  e = cudaGraphInstantiateWithFlags(out, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) *out = nullptr;
   return e;
@@ -177,6 +179,26 @@ ibm_status fold_events(Ctx* h) {
   return IBM_OK;
 }
 
+// CTAs of the correction kernel: one for small boundaries, 3/4 of the SMs
+// above kSmallIbMarkers markers, or the count set by IBM_OPT_IB_CTAS.  A
+// grid of 2..16 CTAs that fits the device as one cluster is launched as a
+// cluster (hardware barrier, CTAs scheduled together).
+void choose_ib_grid(Ctx& c) {
+  const int M = c.nm;
+  // Large boundaries: three CTAs per four SMs.  The correction kernel runs
+  // beside collide+stream and holds its SMs' registers while it runs; on the
+  // 4096^2 Couette step (14052 markers) 3/4 of the SMs gave the shortest step
+  // (the correction chain still ends before collide+stream).
+  const int wide = (3 * c.ib_grid_max + 3) / 4;
+  c.ib_grid = c.ib_grid_opt > 0 ? (c.ib_grid_opt < c.ib_grid_max ? c.ib_grid_opt : c.ib_grid_max)
+                                : (M <= kSmallIbMarkers ? 1 : wide);
+  c.ib_cluster = false;
+  if (c.ib_grid >= 2 && c.ib_grid <= kMaxIbCluster) {
+    if (c.ib_cluster_max < 0) c.ib_cluster_max = ib_max_cluster(c.prec, c.ib_threads);
+    c.ib_cluster = c.ib_grid <= c.ib_cluster_max;
+  }
+}
+
 ibm_status upload_markers(Ctx* h) {
   Ctx& c = *h;
   const int M = c.nm;
@@ -215,8 +237,7 @@ ibm_status upload_markers(Ctx* h) {
   // correction-kernel CTAs: one for small boundaries (its grid barrier is a
   // block barrier, so such kernels of several lattices may run side by
   // side), one per SM otherwise
-  c.ib_grid = c.ib_grid_opt > 0 ? (c.ib_grid_opt < c.ib_grid_max ? c.ib_grid_opt : c.ib_grid_max)
-                                : (M <= kSmallIbMarkers ? 1 : c.ib_grid_max);
+  choose_ib_grid(c);
   c.dbq = dev_alloc(c, R * 8 * (size_t)c.bcap);
   c.dmq = dev_alloc(c, R * 4 * (size_t)M);
   c.dAh = dev_alloc(c, R * 2 * (size_t)M * (c.desc.n_corr + 1));
@@ -815,20 +836,18 @@ ibm_status ibm_set_option(ibm_handle h, int option, long long value) {
       return fail(h, IBM_ERR_INVALID, "the correction kernel cannot be resident with that many threads");
     if (h->stream) cudaStreamSynchronize(h->stream);
     h->ib_threads = (int)value;
+    h->ib_cluster_max = -1;
+    choose_ib_grid(*h);
     destroy_graphs(*h);
     return IBM_OK;
   }
   if (option != IBM_OPT_IB_CTAS) return fail(h, IBM_ERR_INVALID, "unknown option");
   if (value < 0 || value > (1 << 20)) return fail(h, IBM_ERR_INVALID, "IBM_OPT_IB_CTAS out of range");
   h->ib_grid_opt = (int)value;
-  const int M = h->nm;
-  h->ib_grid = h->ib_grid_opt > 0 ? (h->ib_grid_opt < h->ib_grid_max ? h->ib_grid_opt : h->ib_grid_max)
-                                  : (M <= kSmallIbMarkers ? 1 : h->ib_grid_max);
-  {
-    DeviceGuard guard(h->device);
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    destroy_graphs(*h);
-  }
+  DeviceGuard guard(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  choose_ib_grid(*h);
+  destroy_graphs(*h);
   return IBM_OK;
 }
 

@@ -270,7 +270,59 @@ struct IbArgs {
   const double* ds;
   double* fpart;              // [chunks][nb][3]
   unsigned long long* bar;    // grid-barrier arrivals (monotonic)
+  const int* node2band;       // [ny][nx] band index of a node, -1 outside the band
+  int apply;                  // 1: apply the correction here; 0: k_band_collide applies it
+  int cluster;                // 1: launched as one thread-block cluster
 };
+
+// Eq. 27 summed over the iterations at band node b = node (x, y):
+// f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi], with dJ the final spread
+// D^N (bq[6..7]) and dPi = sum over the covering markers of W ds C_l.
+// Read-modify-write of the nine post-stream populations, by one thread.
+template <int P>
+__device__ __forceinline__ void apply_band_correction(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                                      typename Prec<P>::S* __restrict__ A, int parity,
+                                                      const typename Prec<P>::R* __restrict__ bq,
+                                                      const int* __restrict__ bcnt,
+                                                      const Ent<typename Prec<P>::R>* __restrict__ ent,
+                                                      const typename Prec<P>::R* __restrict__ Cm,
+                                                      int b, int x, int y) {
+  typedef typename Prec<P>::R R;
+  R pxx = R(0), pxy = R(0), pyy = R(0);
+  const int cnt = bcnt[b];
+  const Ent<R>* e = ent + (long long)b * kBandCap;
+  for (int k0 = 0; k0 < cnt; k0 += 8) {
+    Ent<R> q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (k0 + j < cnt) q[j] = e[k0 + j];
+      else { q[j].m = 0; q[j].w = R(0); }
+    }
+    R c0[8], c1[8], c2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c0[j] = Cm[3 * q[j].m];
+      c1[j] = Cm[3 * q[j].m + 1];
+      c2[j] = Cm[3 * q[j].m + 2];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      pxx += q[j].w * c0[j];
+      pxy += q[j].w * c1[j];
+      pyy += q[j].w * c2[j];
+    }
+  }
+  const R jx = bq[8 * b + 6], jy = bq[8 * b + 7];
+  long long where;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    post_stream<P>(g, c, A, parity, x, y, i, where);
+    if (where < 0) continue;
+    const int slot = (int)(where / g.plane);
+    const R df = feq_i<R>(i, R(0), jx, jy, pxx, pxy, pyy);
+    A[where] = Prec<P>::st(Prec<P>::ld(A[where], slot) + df, slot);
+  }
+}
 
 // Grid barrier for a launch whose CTAs are all resident (one per SM).  A
 // 64-bit arrival counter only grows: the k-th barrier of all launches is
@@ -280,7 +332,7 @@ struct IbArgs {
 // per-warp maxima in red[] are combined first and folded into *dst.
 template <class R>
 __device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr, const R* red = nullptr,
-                                             R* dst = nullptr) {
+                                             R* dst = nullptr, int cluster = 0) {
   __syncthreads();
   if (threadIdx.x == 0 && dst) {
     R m = red[0];
@@ -289,6 +341,13 @@ __device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr, 
   }
   if (gridDim.x == 1) {                           // one CTA: a block barrier suffices
     __syncthreads();
+    return;
+  }
+  if (cluster) {                                  // one cluster: the hardware cluster barrier
+    // release orders this CTA's global writes before the arrival; acquire
+    // makes the other CTAs' writes visible after the wait
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
     return;
   }
   if (threadIdx.x == 0) {
@@ -361,30 +420,32 @@ __device__ __forceinline__ void sparse_dot(const Ent<R>* __restrict__ e, int n, 
   }
 }
 
-// Same sum for a stored row of at least 8 slots whose length is read from
-// cntp: the first eight entries are loaded together with the length, so the
-// common short row costs two dependent memory trips.
+// Same sum for a stored row of at least kRowHead slots whose length is read
+// from cntp: the first kRowHead entries are loaded together with the length,
+// so a row of up to kRowHead entries (every row of a ring of markers one
+// lattice unit apart: 7 to 10) costs two dependent memory trips.
+constexpr int kRowHead = 10;
 template <class R>
 __device__ __forceinline__ void row_dot(const Ent<R>* __restrict__ e, const int* __restrict__ cntp,
                                         const R* __restrict__ A, int pad_m, R& sx, R& sy) {
   typedef typename Vec2<R>::T V;
   const V* Av = reinterpret_cast<const V*>(A);
-  Ent<R> q[8];
+  Ent<R> q[kRowHead];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) q[j] = e[j];
+  for (int j = 0; j < kRowHead; ++j) q[j] = e[j];
   const int n = *cntp;
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
+  for (int j = 0; j < kRowHead; ++j)
     if (j >= n) { q[j].m = pad_m; q[j].w = R(0); }
-  V v[8];
+  V v[kRowHead];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = Av[q[j].m];
+  for (int j = 0; j < kRowHead; ++j) v[j] = Av[q[j].m];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < kRowHead; ++j) {
     sx += q[j].w * v[j].x;
     sy += q[j].w * v[j].y;
   }
-  if (n > 8) sparse_dot<R>(e + 8, n - 8, A, pad_m, sx, sy);
+  if (n > kRowHead) sparse_dot<R>(e + kRowHead, n - kRowHead, A, pad_m, sx, sy);
 }
 
 // dj = b_l - sum_m G_lm A_m for marker l (row in ascending m).
@@ -420,7 +481,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
     a.bq[8 * b + 1] = jx;
     a.bq[8 * b + 2] = jy;
   }
-  grid_barrier<R>(a.bar, a.ctr);
+  grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster);
 
   // phase 0: interpolate rho*, J*^0 (Eq. 22b with Eq. 28 in moment form),
   // b_l = rho* U_l - J*^0 and A^1 = b (A^0 = 0); band nodes: S2 = j^0 j^0
@@ -456,7 +517,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
     }
     warp_max_to<R>(rmax, red);
   }
-  grid_barrier<R>(a.bar, a.ctr, red, a.resid);
+  grid_barrier<R>(a.bar, a.ctr, red, a.resid, a.cluster);
 
   // phases 1..N-1: Jacobi iteration A^{n+1} = A^n + b - G A^n; band nodes
   // add j^n j^n to S2
@@ -472,7 +533,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
     }
     warp_max_to<R>(rmax, red);
-    grid_barrier<R>(a.bar, a.ctr, red, a.resid + n);
+    grid_barrier<R>(a.bar, a.ctr, red, a.resid + n, a.cluster);
   }
 
   // final phase: residual r^N; per band node the final spread D^N and
@@ -501,24 +562,43 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       for (int j = 0; j < 8; ++j)
         if (j >= cnt) { q[j].m = 0; q[j].w = R(0); }
       R sxx = R(0), sxy = R(0), syy = R(0), dx = R(0), dy = R(0);
-      for (int n = 0; n <= N; ++n) {
+      // two levels per trip: the sixteen A loads of n and n + 1 are in
+      // flight together (sums per level in list order, as one level alone)
+      for (int n = 0; n <= N; n += 2) {
+        const bool two = n + 1 <= N;
         const R* An = a.Ah + (long long)n * 2 * M;
+        const R* Bn = two ? An + 2 * M : An;
         const V* Av = reinterpret_cast<const V*>(An);
-        V v[8];
+        const V* Bv = reinterpret_cast<const V*>(Bn);
+        V v[8], u[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = Av[q[j].m];
-        R px = R(0), py = R(0);
+        for (int j = 0; j < 8; ++j) {
+          v[j] = Av[q[j].m];
+          u[j] = Bv[q[j].m];
+        }
+        R px = R(0), py = R(0), ox = R(0), oy = R(0);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           px += q[j].w * v[j].x;
           py += q[j].w * v[j].y;
+          ox += q[j].w * u[j].x;
+          oy += q[j].w * u[j].y;
         }
-        if (cnt > 8) sparse_dot<R>(e + 8, cnt - 8, An, 0, px, py);
-        if (n < N) {
-          const R jx = j0x + px, jy = j0y + py;
-          sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
-        } else {
-          dx = px; dy = py;
+        if (cnt > 8) {
+          sparse_dot<R>(e + 8, cnt - 8, An, 0, px, py);
+          if (two) sparse_dot<R>(e + 8, cnt - 8, Bn, 0, ox, oy);
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int lv = n + t;
+          if (lv > N) break;
+          const R qx = t == 0 ? px : ox, qy = t == 0 ? py : oy;
+          if (lv < N) {
+            const R jx = j0x + qx, jy = j0y + qy;
+            sxx += jx * jx; sxy += jx * jy; syy += jy * jy;
+          } else {
+            dx = qx; dy = qy;
+          }
         }
       }
       a.bq[8 * b + 3] = sxx;
@@ -528,7 +608,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       a.bq[8 * b + 7] = dy;
     }
   }
-  grid_barrier<R>(a.bar, a.ctr, red, a.resid + N);
+  grid_barrier<R>(a.bar, a.ctr, red, a.resid + N, a.cluster);
 
   // second-moment deviations summed over the iterations:
   // C_l = N rho* U U - sum_x W_l(x) / rho(x) sum_n j^n j^n
@@ -556,46 +636,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       a.Cm[3 * l + 2] = R(N) * rs * uy * uy - pyy;
     }
   }
-  grid_barrier<R>(a.bar, a.ctr);
+  if (a.apply) grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster);     // the apply reads every C_l
 
-  // Eq. 27 summed over the iterations: f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi]
-  if (N > 0) {
+  // Eq. 27 summed over the iterations, unless k_band_collide applies it
+  // just before it streams the band segments
+  if (N > 0 && a.apply) {
     for (int b = tid; b < nband; b += nth) {
-      R pxx = R(0), pxy = R(0), pyy = R(0);
-      const int cnt = a.bcnt[b];
-      const Ent<R>* e = a.ent + (long long)b * kBandCap;
-      for (int k0 = 0; k0 < cnt; k0 += 8) {
-        Ent<R> q[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          if (k0 + j < cnt) q[j] = e[k0 + j];
-          else { q[j].m = 0; q[j].w = R(0); }
-        }
-        R c0[8], c1[8], c2[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          c0[j] = a.Cm[3 * q[j].m];
-          c1[j] = a.Cm[3 * q[j].m + 1];
-          c2[j] = a.Cm[3 * q[j].m + 2];
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          pxx += q[j].w * c0[j];
-          pxy += q[j].w * c1[j];
-          pyy += q[j].w * c2[j];
-        }
-      }
-      const R jx = a.bq[8 * b + 6], jy = a.bq[8 * b + 7];
       const int n = a.bnode[b];
-      const int x = n % a.g.nx, y = n / a.g.nx;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        post_stream<P>(a.g, a.c, a.A, PAR, x, y, i, where);
-        if (where < 0) continue;
-        const int slot = (int)(where / a.g.plane);
-        const R df = feq_i<R>(i, R(0), jx, jy, pxx, pxy, pyy);
-        a.A[where] = Prec<P>::st(Prec<P>::ld(a.A[where], slot) + df, slot);
-      }
+      apply_band_correction<P>(a.g, a.c, a.A, PAR, a.bq, a.bcnt, a.ent, a.Cm, b, n % a.g.nx, n / a.g.nx);
     }
   }
 
@@ -626,7 +674,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       }
     }
   }
-  grid_barrier<R>(a.bar, a.ctr);
+  grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster);
 
   // body totals: one body per CTA, fixed-shape reduction over the chunks
   for (int bd = blockIdx.x; bd < a.nb; bd += gridDim.x) {
@@ -649,18 +697,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
 // Collide+stream of the 32-node row segments that hold band nodes, after
 // the correction kernel has corrected them: one warp per segment.
 template <int P, int PAR, bool MACRO, bool MRT>
-__global__ void __launch_bounds__(256) k_band_collide(Geom g, StepConsts<typename Prec<P>::R> c,
-                                                      typename Prec<P>::S* __restrict__ A,
-                                                      typename Prec<P>::R* __restrict__ mac,
-                                                      const int* __restrict__ seglist,
-                                                      const int* __restrict__ ctr, int nseg_x) {
-  const int nseg = ctr[CTR_NSEG];
+__global__ void __launch_bounds__(256) k_band_collide(IbArgs<P> a) {
+  const Geom& g = a.g;
+  const StepConsts<typename Prec<P>::R>& c = a.c;
+  typename Prec<P>::S* __restrict__ A = a.A;
+  typename Prec<P>::R* __restrict__ mac = a.mac;
+  const int nseg_x = a.nseg_x;
+  const int nseg = a.ctr[CTR_NSEG];
   const int lane = threadIdx.x & (kSegW - 1);
   const int nw = (gridDim.x * blockDim.x) / kSegW;
   for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / kSegW; k < nseg; k += nw) {
-    const int seg = seglist[k];
+    const int seg = a.seglist[k];
     const int y = seg / nseg_x, x = (seg % nseg_x) * kSegW + lane;
     if (x >= g.nx) continue;
+    // Eq. 27 at a band node first (the same thread then reads the node's
+    // corrected populations; they are its own slots)
+    if (!a.apply && a.N > 0) {
+      const int b = a.node2band[y * g.nx + x];
+      if (b >= 0) apply_band_correction<P>(g, c, A, PAR, a.bq, a.bcnt, a.ent, a.Cm, b, x, y);
+    }
     if (PAR == 0) even_node<P, MACRO, MRT>(g, c, A, mac, x, y);
     else odd_node<P, MACRO, MRT>(g, c, A, mac, x, y);
   }
@@ -775,15 +830,27 @@ void launch_band_build(const Ctx& h, cudaStream_t s) {
   else band_build_t<float>(h, s);
 }
 
+template <int P, int NT>
+static void launch_ib(int parity, bool cluster, dim3 grid, dim3 block, cudaStream_t s, int prio,
+                      const IbArgs<P>& a) {
+  if (cluster) {
+    if (parity == 0) launch_prio_cluster(k_ib_step<P, 0, NT>, grid, block, s, prio, a);
+    else launch_prio_cluster(k_ib_step<P, 1, NT>, grid, block, s, prio, a);
+  } else {
+    if (parity == 0) launch_prio(k_ib_step<P, 0, NT>, grid, block, s, prio, a);
+    else launch_prio(k_ib_step<P, 1, NT>, grid, block, s, prio, a);
+  }
+}
+
 template <int P, bool MRT>
 static void launch_band_collide(dim3 g2, dim3 b2, cudaStream_t s, int prio, const IbArgs<P>& a,
-                                const int* ctr, int parity, bool macro) {
+                                int parity, bool macro) {
   if (parity == 0) {
-    if (macro) launch_prio(k_band_collide<P, 0, true, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
-    else launch_prio(k_band_collide<P, 0, false, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+    if (macro) launch_prio(k_band_collide<P, 0, true, MRT>, g2, b2, s, prio, a);
+    else launch_prio(k_band_collide<P, 0, false, MRT>, g2, b2, s, prio, a);
   } else {
-    if (macro) launch_prio(k_band_collide<P, 1, true, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
-    else launch_prio(k_band_collide<P, 1, false, MRT>, g2, b2, s, prio, a.g, a.c, a.A, a.mac, a.seglist, ctr, a.nseg_x);
+    if (macro) launch_prio(k_band_collide<P, 1, true, MRT>, g2, b2, s, prio, a);
+    else launch_prio(k_band_collide<P, 1, false, MRT>, g2, b2, s, prio, a);
   }
 }
 
@@ -825,28 +892,27 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   a.ds = h.dds;
   a.fpart = h.dfpart;
   a.bar = h.dbar;
+  a.node2band = h.dnode2band;
+  a.apply = h.band_collide ? 0 : 1;
+  a.cluster = (h.ib_cluster && h.ib_grid > 1) ? 1 : 0;
   cudaMemsetAsync(h.dresid, 0, sizeof(R) * (a.N + 1), s);
   const dim3 grid(h.ib_grid), block(h.ib_threads);
   switch (h.ib_threads) {
     case 512:
-      if (parity == 0) launch_prio(k_ib_step<P, 0, 512>, grid, block, s, h.ib_prio, a);
-      else launch_prio(k_ib_step<P, 1, 512>, grid, block, s, h.ib_prio, a);
+      launch_ib<P, 512>(parity, a.cluster != 0, grid, block, s, h.ib_prio, a);
       break;
     case 1024:
-      if (parity == 0) launch_prio(k_ib_step<P, 0, 1024>, grid, block, s, h.ib_prio, a);
-      else launch_prio(k_ib_step<P, 1, 1024>, grid, block, s, h.ib_prio, a);
+      launch_ib<P, 1024>(parity, a.cluster != 0, grid, block, s, h.ib_prio, a);
       break;
     default:
-      if (parity == 0) launch_prio(k_ib_step<P, 0, kIbThreads>, grid, block, s, h.ib_prio, a);
-      else launch_prio(k_ib_step<P, 1, kIbThreads>, grid, block, s, h.ib_prio, a);
+      launch_ib<P, kIbThreads>(parity, a.cluster != 0, grid, block, s, h.ib_prio, a);
   }
   // the band segments, once corrected
   if (h.band_collide) {
     const int need = (h.segcap * kSegW + 255) / 256;
     const dim3 g2(need < 8 * h.ib_grid_max ? (need > 0 ? need : 1) : 8 * h.ib_grid_max), b2(256);
-    const int* ctr = a.ctr;
-    if (a.c.mrt) launch_band_collide<P, true>(g2, b2, s, h.ib_prio, a, ctr, parity, macro);
-    else launch_band_collide<P, false>(g2, b2, s, h.ib_prio, a, ctr, parity, macro);
+    if (a.c.mrt) launch_band_collide<P, true>(g2, b2, s, h.ib_prio, a, parity, macro);
+    else launch_band_collide<P, false>(g2, b2, s, h.ib_prio, a, parity, macro);
   }
 }
 
@@ -886,6 +952,62 @@ int ib_blocks_per_sm(int prec, int threads) {
     case PREC_FP32: return ib_blocks_per_sm_t<PREC_FP32>(threads);
     case PREC_FP16_DEV: return ib_blocks_per_sm_t<PREC_FP16_DEV>(threads);
     default: return ib_blocks_per_sm_t<PREC_BF16_DEV>(threads);
+  }
+}
+
+template <int P, int NT>
+static int max_cluster_nt() {
+  int best = 0;
+  for (int k = 0; k < 2; ++k) {
+    void (*kern)(IbArgs<P>) = k == 0 ? k_ib_step<P, 0, NT> : k_ib_step<P, 1, NT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
+  for (int c = kMaxIbCluster; c >= 2; --c) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(NT);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n0 = 0, n1 = 0;
+    if (cudaOccupancyMaxActiveClusters(&n0, k_ib_step<P, 0, NT>, &cfg) != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&n1, k_ib_step<P, 1, NT>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (n0 > 0 && n1 > 0) { best = c; break; }
+  }
+  return best;
+}
+
+template <int P>
+static int max_cluster_t(int threads) {
+  switch (threads) {
+    case 512: return max_cluster_nt<P, 512>();
+    case 1024: return max_cluster_nt<P, 1024>();
+    default: return max_cluster_nt<P, kIbThreads>();
+  }
+}
+
+int ib_max_cluster(int prec, int threads) {
+  int dev = 0, ok = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, dev) != cudaSuccess || !ok) {
+    cudaGetLastError();
+    return 0;
+  }
+  switch (prec) {
+    case PREC_FP64: return max_cluster_t<PREC_FP64>(threads);
+    case PREC_FP32: return max_cluster_t<PREC_FP32>(threads);
+    case PREC_FP16_DEV: return max_cluster_t<PREC_FP16_DEV>(threads);
+    default: return max_cluster_t<PREC_BF16_DEV>(threads);
   }
 }
 

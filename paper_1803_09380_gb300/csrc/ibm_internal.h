@@ -112,6 +112,8 @@ struct Ctx {
   int ib_grid = 0;                           // CTAs of the correction kernel
   int ib_grid_max = 0;                       // one per SM
   int ib_threads = kIbThreads;               // threads per correction-loop CTA: 256, 512, 1024
+  bool ib_cluster = false;                   // launch the correction kernel as one cluster
+  int ib_cluster_max = -1;                   // largest schedulable cluster (-1: not yet asked)
   int ib_grid_opt = 0;                       // caller's choice (IBM_OPT_IB_CTAS), 0 = by size
   bool band_collide = true;                  // stream the band segments after the correction
   bool band_valid = false;
@@ -199,6 +201,29 @@ inline void launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStr
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// The same launch as one thread-block cluster of grid.x CTAs: the hardware
+// schedules the cluster's CTAs together, so a barrier across them can never
+// wait for a CTA that is not resident.
+template <typename... KArgs, typename... Args>
+inline void launch_prio_cluster(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, int prio,
+                                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = grid.x;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ibm_api.cu
 void set_thread_error(const char* msg);
 // ibm_create_lattice with an optional memory pool: when pool is not NULL
@@ -214,6 +239,11 @@ void launch_fields(const Ctx& h, int op, const double* dev_in, double* dev_out, 
 void launch_band_build(const Ctx& h, cudaStream_t s);
 void launch_ib_loop(const Ctx& h, int parity, bool macro, cudaStream_t s);
 int ib_blocks_per_sm(int prec, int threads = kIbThreads);
+// Largest number of correction-kernel CTAs (at most kMaxIbCluster) that the
+// device can schedule as one cluster; 0 when cluster launches are not
+// available.
+int ib_max_cluster(int prec, int threads);
+constexpr int kMaxIbCluster = 16;
 void launch_body_update(const Ctx& h, cudaStream_t s);
 
 }  // namespace ibm

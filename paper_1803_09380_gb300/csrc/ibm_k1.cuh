@@ -9,6 +9,8 @@
 
 namespace ibm {
 
+constexpr int kOddVecDiv = 1;   // odd-step nodes per lane = even-step nodes per lane / this
+
 template <class R>
 __device__ __forceinline__ void bgk(const R* p, R* ps, R& rho, R& jx, R& jy, R omega) {
   moments9(p, rho, jx, jy);
@@ -177,9 +179,13 @@ template <int P>
 struct VecTraits {
   typedef typename Prec<P>::S S;
   static constexpr int VEC = sizeof(S) == 8 ? 2 : 4;
+  // nodes per lane in the odd step (fewer live values per thread there)
+  static constexpr int VEC_ODD = VEC / kOddVecDiv;
 };
 
 template <int BYTES> struct VecWord;
+template <> struct VecWord<2> { typedef unsigned short T; };
+template <> struct VecWord<4> { typedef unsigned int T; };
 template <> struct VecWord<8> { typedef uint2 T; };
 template <> struct VecWord<16> { typedef uint4 T; };
 
@@ -276,7 +282,7 @@ __device__ __forceinline__ void odd_vec(const Geom& g, const StepConsts<typename
                                         bool skip) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
-  constexpr int VEC = VecTraits<P>::VEC;
+  constexpr int VEC = VecTraits<P>::VEC_ODD;
   const int xl = x0 == 0 ? g.nx - 1 : x0 - 1;              // left of the lane's nodes
   const int xr = x0 + VEC == g.nx ? 0 : x0 + VEC;           // right of the lane's nodes
   const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;

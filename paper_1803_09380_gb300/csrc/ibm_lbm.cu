@@ -34,12 +34,14 @@ namespace ibm {
 // step: spans without boundary or ragged nodes take the vector path (lanes
 // whose nodes lie in band segments sit out); the others go node by node
 // through the boundary-aware path.
+constexpr int kK1Threads = 256;   // threads per collide+stream block (whole warps per row span)
+
 template <int P, int PAR, bool MACRO, int MODE, bool MRT>
-__global__ void __launch_bounds__(256) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
+__global__ void __launch_bounds__(kK1Threads) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
                                                         typename Prec<P>::S* __restrict__ A,
                                                         typename Prec<P>::R* __restrict__ mac,
                                                         const int* __restrict__ segflag, int nseg_x) {
-  constexpr int VEC = VecTraits<P>::VEC;
+  constexpr int VEC = PAR ? VecTraits<P>::VEC_ODD : VecTraits<P>::VEC;
   const int lane = threadIdx.x & 31;
   const int y = blockIdx.y;
   const int xw = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * VEC);
@@ -163,14 +165,15 @@ static void launch_k1(const Ctx& h, const StepConsts<typename Prec<P>::R>& c, in
   typedef typename Prec<P>::R R;
   S* A = (S*)h.f;
   R* mac = (R*)h.macro;
-  constexpr int VEC = VecTraits<P>::VEC;
+  constexpr int VEC = PAR ? VecTraits<P>::VEC_ODD : VecTraits<P>::VEC;
   const int warps_per_row = (h.geom.nx + 32 * VEC - 1) / (32 * VEC);
-  const dim3 grid((warps_per_row + 7) / 8, h.geom.ny);
+  constexpr int wpb = kK1Threads / 32;
+  const dim3 grid((warps_per_row + wpb - 1) / wpb, h.geom.ny);
   if (mode == K1_MAIN) {
-    k_collide_stream<P, PAR, MACRO, K1_MAIN, MRT><<<grid, 256, 0, s>>>(
+    k_collide_stream<P, PAR, MACRO, K1_MAIN, MRT><<<grid, kK1Threads, 0, s>>>(
         h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   } else {
-    k_collide_stream<P, PAR, MACRO, K1_ALL, MRT><<<grid, 256, 0, s>>>(
+    k_collide_stream<P, PAR, MACRO, K1_ALL, MRT><<<grid, kK1Threads, 0, s>>>(
         h.geom, c, A, mac, h.dsegflag, h.nseg_x);
   }
 }

@@ -46,6 +46,7 @@ struct CaseRec {
   unsigned outputs = 0;
   double bytes = 0.0;
   int ib_ctas = 1;
+  int ib_budget = 0;          // CTAs counted against the budget (grid-barrier launches only)
   ibm_handle h = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};   // ring of chunk-completion events
@@ -76,14 +77,14 @@ double case_bytes(const ibm_lattice_desc& d, int M, int nb) {
 }
 
 // Correction-loop CTAs of a served case: one CTA per `per_cta` markers, at
-// most one per SM.  Fewer CTAs than the stand-alone default (one per SM)
-// keep each case's grid barrier cheap and let many cases' correction
-// kernels be resident at once.
+// most ibm::kMaxIbCluster, so that every multi-CTA correction kernel can run
+// as one thread-block cluster (CTAs scheduled together, hardware barrier)
+// and many cases' correction kernels are resident at once.
 constexpr int kServeMarkersPerCta = 512;
-int server_ib_ctas(int M, int sms, int per_cta) {
+int server_ib_ctas(int M, int per_cta) {
   if (M == 0) return 0;
   if (per_cta <= 0) per_cta = kServeMarkersPerCta;
-  return std::max(1, std::min(sms, (M + per_cta - 1) / per_cta));
+  return std::max(1, std::min(ibm::kMaxIbCluster, (M + per_cta - 1) / per_cta));
 }
 
 }  // namespace
@@ -99,6 +100,7 @@ struct ibm_server_s {
   std::vector<cudaStream_t> streams;       // idle streams for reuse
   std::vector<cudaEvent_t> events;
   cudaMemPool_t pool = nullptr;
+  int max_cluster[4] = {-1, -1, -1, -1};     // per precision, from ibm::ib_max_cluster
   double bytes_in_use = 0.0;
   int ctas_in_use = 0;
   long long next_id = 1;
@@ -131,7 +133,7 @@ void release_device(ibm_server s, CaseRec* c) {
   for (auto& e : c->ev)
     if (e) { s->events.push_back(e); e = nullptr; }
   s->bytes_in_use -= c->bytes;
-  s->ctas_in_use -= c->ib_ctas;
+  s->ctas_in_use -= c->ib_budget;
   s->active.erase(std::remove(s->active.begin(), s->active.end(), c->id), s->active.end());
 }
 
@@ -270,6 +272,8 @@ ibm_status ibm_server_submit(ibm_server s, const ibm_case_desc* c, long long* ca
   if (!s) return sfail(nullptr, IBM_ERR_INVALID, "server is NULL");
   if (!c || c->nsteps < 0 || c->nbodies < 0 || (c->nbodies > 0 && (!c->bodies || !c->nmarkers || !c->xy)))
     return sfail(s, IBM_ERR_INVALID, "invalid case description");
+  if (c->lattice.prec < IBM_FP64 || c->lattice.prec > IBM_BF16_DEV)
+    return sfail(s, IBM_ERR_INVALID, "unknown precision");
   try {
     CaseRec* r = new CaseRec();
     r->id = s->next_id++;
@@ -286,7 +290,20 @@ ibm_status ibm_server_submit(ibm_server s, const ibm_case_desc* c, long long* ca
     r->xy.assign(c->xy ? c->xy : nullptr, c->xy ? c->xy + 2 * (size_t)M : nullptr);
     if (c->ds) { r->ds.assign(c->ds, c->ds + M); r->has_ds = true; }
     r->bytes = case_bytes(c->lattice, M, c->nbodies);
-    r->ib_ctas = server_ib_ctas(M, s->sms, s->desc.ib_markers_per_cta);
+    r->ib_ctas = server_ib_ctas(M, s->desc.ib_markers_per_cta);
+    if (r->ib_ctas >= 2) {
+      // a grid that cannot be scheduled as one cluster falls back to the
+      // grid barrier, whose CTAs must all be resident: count those
+      const int p = c->lattice.prec;
+      if (s->max_cluster[p] < 0) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(s->desc.device);
+        s->max_cluster[p] = ibm::ib_max_cluster(p, ibm::kIbThreads);
+        cudaSetDevice(prev);
+      }
+      r->ib_budget = r->ib_ctas <= s->max_cluster[p] ? 0 : r->ib_ctas;
+    }
     r->t_submit = now_s();
     if (s->t_first < 0) s->t_first = r->t_submit;
     s->cases[r->id] = r;
@@ -352,12 +369,12 @@ ibm_status ibm_server_progress(ibm_server s, int* completed) {
     const bool empty = s->active.empty();
     if ((int)s->active.size() >= s->desc.max_active) break;
     if (!empty && s->bytes_in_use + c->bytes > s->budget) break;
-    if (!empty && s->ctas_in_use + c->ib_ctas > s->cta_budget) break;
+    if (!empty && s->ctas_in_use + c->ib_budget > s->cta_budget) break;
     s->pending.pop_front();
     c->state = CASE_ACTIVE;
     s->active.push_back(c->id);
     s->bytes_in_use += c->bytes;
-    s->ctas_in_use += c->ib_ctas;
+    s->ctas_in_use += c->ib_budget;
     const double t0 = now_s();
     ibm_status st = admit(s, c);
     s->t_admit += now_s() - t0;
