@@ -60,25 +60,40 @@ __host__ __device__ constexpr R wgt(int i) {
 // S is the stored type of one population, R the arithmetic type.  The
 // 16-bit forms keep f_i - w_i (the deviation from the rest weight).
 template <int P> struct Prec;
+// ld/st convert between storage and the full population f_i; ldv/stv are
+// the vector kernels' forms, which keep the stored variable (kDev: the
+// deviation f_i - w_i for 16-bit storage, f_i otherwise).
 template <> struct Prec<PREC_FP64> {
   typedef double S; typedef double R;
+  static constexpr bool kDev = false;
   static __device__ __forceinline__ R ld(S v, int) { return v; }
   static __device__ __forceinline__ S st(R v, int) { return v; }
+  static __device__ __forceinline__ R ldv(S v, int) { return v; }
+  static __device__ __forceinline__ S stv(R v, int) { return v; }
 };
 template <> struct Prec<PREC_FP32> {
   typedef float S; typedef float R;
+  static constexpr bool kDev = false;
   static __device__ __forceinline__ R ld(S v, int) { return v; }
   static __device__ __forceinline__ S st(R v, int) { return v; }
+  static __device__ __forceinline__ R ldv(S v, int) { return v; }
+  static __device__ __forceinline__ S stv(R v, int) { return v; }
 };
 template <> struct Prec<PREC_FP16_DEV> {
   typedef __half S; typedef float R;
+  static constexpr bool kDev = true;
   static __device__ __forceinline__ R ld(S v, int i) { return wgt<float>(i) + __half2float(v); }
   static __device__ __forceinline__ S st(R v, int i) { return __float2half_rn(v - wgt<float>(i)); }
+  static __device__ __forceinline__ R ldv(S v, int) { return __half2float(v); }
+  static __device__ __forceinline__ S stv(R v, int) { return __float2half_rn(v); }
 };
 template <> struct Prec<PREC_BF16_DEV> {
   typedef __nv_bfloat16 S; typedef float R;
+  static constexpr bool kDev = true;
   static __device__ __forceinline__ R ld(S v, int i) { return wgt<float>(i) + __bfloat162float(v); }
   static __device__ __forceinline__ S st(R v, int i) { return __float2bfloat16_rn(v - wgt<float>(i)); }
+  static __device__ __forceinline__ R ldv(S v, int) { return __bfloat162float(v); }
+  static __device__ __forceinline__ S stv(R v, int) { return __float2bfloat16_rn(v); }
 };
 
 // ----------------------------------------------------------------- geometry
