@@ -234,6 +234,23 @@ def measured_traffic(prec: str, n: int):
     return t[0], t[2]
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks: a replica job takes as long as its
+    slowest rank.  dist is torch.distributed (or None for one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes: int, steps: int, world: int, ms: float) -> float:
+    """Lattice updates of all replicas over the job's time (weak scaling:
+    every rank runs the same lattice)."""
+    return nodes * steps * world / (ms * 1e-3) / 1e6
+
+
 def run_ours(args, rank, world, local_rank, dist):
     import numpy as np
     import torch
@@ -277,11 +294,8 @@ def run_ours(args, rank, world, local_rank, dist):
     k1_ms, k1_n = lat.kernel_times()
     l1, _ = lat.counters()
     launches = l1 - l0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N2 * args.steps * world / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_mlups(N2, args.steps, world, ms)
 
     peak, peak_src = measured_peak_hbm()
     bytes_per_update = 18 * BYTES_PER_POP[args.prec]
@@ -397,11 +411,8 @@ def run_e2e(args, case, local_rank, dist, world):
         lat.read(fld, out=o.numpy())
     dt = time.perf_counter() - t0
     lat.close()
-    if dist is not None:
-        tt = torch.tensor([dt], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-    return {"value": nx * ny * args.steps * world / dt / 1e6, "unit": "MLUPS",
+    dt = max_over_ranks(dt, dist, "cuda")
+    return {"value": whole_job_mlups(nx * ny, args.steps, world, dt * 1e3), "unit": "MLUPS",
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
             "wall_s": dt,
             "what": "create lattice + upload markers (pinned) + steps + read rho, ux, uy (pinned)"}
