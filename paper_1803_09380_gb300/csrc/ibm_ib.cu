@@ -84,8 +84,11 @@ __global__ void k_band_clear(Geom g, const int* __restrict__ ctr, const int* __r
 template <class R>
 __global__ void k_band_claim(Geom g, int M, const double* __restrict__ X, const double* __restrict__ Y,
                              R* __restrict__ W, int* __restrict__ node_of, int* __restrict__ node2band,
-                             int* __restrict__ claim, int points) {
+                             int* __restrict__ claim, int points, int* __restrict__ ctr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // reset the band and segment counts (k_band_clear, the previous launch,
+  // has read them; k_band_alloc, the next, counts from zero)
+  if (t == 0) { ctr[CTR_NBAND] = 0; ctr[CTR_NSEG] = 0; }
   if (t >= M * kStencil) return;
   const int l = t / kStencil, s = t % kStencil;
   const double Xl = X[l], Yl = Y[l];
@@ -469,6 +472,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
   const int M = a.M, N = a.N;
   long long where;
 
+  // residual history of this step starts at zero (first read-modify-write
+  // after the next barrier)
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k <= N; k += blockDim.x) a.resid[k] = R(0);
+
   // gather rho and j^0 at every band node
   for (int b = tid; b < nband; b += nth) {
     const int n = a.bnode[b];
@@ -811,9 +819,8 @@ static void band_build_t(const Ctx& h, cudaStream_t s) {
   if (T == 0) return;
   k_band_clear<<<blocks_for(h.bcap, 256), 256, 0, s>>>(h.geom, h.dctr, h.dbnode, h.dnode2band,
                                                         h.dsegflag, h.nseg_x, h.bcap);
-  cudaMemsetAsync(h.dctr, 0, 2 * sizeof(int), s);   // band nodes, band segments
   k_band_claim<R><<<blocks_for(T, 256), 256, 0, s>>>(h.geom, h.nm, h.dX, h.dY, (R*)h.dW, h.dnode_of,
-                                                      h.dnode2band, h.dclaim, h.desc.delta_points);
+                                                      h.dnode2band, h.dclaim, h.desc.delta_points, h.dctr);
   k_band_alloc<<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, h.dclaim, h.dnode2band, h.dbnode,
                                                   h.dbcnt, h.dctr, h.bcap);
   k_band_fill<R><<<blocks_for(T, 256), 256, 0, s>>>(h.nm, h.dnode_of, (const R*)h.dW, h.dds, h.dnode2band,
@@ -895,7 +902,6 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   a.node2band = h.dnode2band;
   a.apply = h.band_collide ? 0 : 1;
   a.cluster = (h.ib_cluster && h.ib_grid > 1) ? 1 : 0;
-  cudaMemsetAsync(h.dresid, 0, sizeof(R) * (a.N + 1), s);
   const dim3 grid(h.ib_grid), block(h.ib_threads);
   switch (h.ib_threads) {
     case 512:
