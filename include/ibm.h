@@ -70,7 +70,16 @@ typedef enum {
   IBM_BC_BOUNCEBACK = 1,      /* half-way bounce-back, optional wall velocity */
   IBM_BC_FREESLIP = 2,        /* specular reflection */
   IBM_BC_INLET_EQ = 3,
-  IBM_BC_OUTLET_ZEROGRAD = 4
+  IBM_BC_OUTLET_ZEROGRAD = 4,
+  IBM_BC_INLET_NEE = 5,       /* -x side only: velocity inlet by non-equilibrium
+                                 extrapolation (the scheme of section 3.2):
+                                 column 0 is rebuilt every step as
+                                 f^eq(rho(1), inlet_u) + f(1) - f^eq(rho(1), u(1)) */
+  IBM_BC_OUTLET_NEE = 6       /* +x side only: pressure outlet by the same
+                                 extrapolation, column nx-1 rebuilt as
+                                 f^eq(rho0, u(nx-2)) + f(nx-2) - f^eq(nx-2);
+                                 marker supports must stay off the two
+                                 columns next to an extrapolation side */
 } ibm_bc;
 
 /* Collision operator.  BGK: Omega_i = -(f_i - f_i^eq)/tau.  MRT: Eq. 2

@@ -19,6 +19,9 @@ Parity status of the functions (what pins each one is in ``tests/``):
                                   Galilean advection of the wave
   walls (bounce-back, free-slip)  pinned by plane Poiseuille / plug flow
   inlet / outlet                  pinned by uniform-flow preservation
+  extrapolation inlet / outlet    pinned by uniform-flow preservation, the
+                                  exact rebuild of an equilibrium neighbour
+                                  and plane Poiseuille flow
   whole step                      pinned by the analytic Couette profile
                                   (Eq. 34) and its measured convergence slope
   MRT collision (Eqs. 2, 5, 6)    pinned by the closed-form equilibrium
@@ -45,6 +48,7 @@ _lock = threading.Lock()
 _lib = None
 
 PERIODIC, BOUNCEBACK, FREESLIP, INLET_EQ, OUTLET_ZEROGRAD = 0, 1, 2, 3, 4
+INLET_NEE, OUTLET_NEE = 5, 6
 BODY_FIXED, BODY_PRESCRIBED, BODY_FREE = 0, 1, 2
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -90,7 +94,7 @@ def _load():
         lib.ora_add_body.restype = ctypes.c_int
         lib.ora_add_body.argtypes = [vp, ctypes.c_int, _D, _D, _D, ctypes.c_int]
         for name in ("ora_ib_correct", "ora_move_bodies", "ora_record_moments",
-                     "ora_collide_stream"):
+                     "ora_collide_stream", "ora_open_boundaries"):
             getattr(lib, name).argtypes = [vp]
         lib.ora_step.argtypes = [vp, ctypes.c_int]
         for name in ("ora_get_f", "ora_set_f", "ora_get_resid", "ora_get_bodies",
@@ -223,6 +227,9 @@ class Lattice:
 
     def move_bodies(self):
         self._lib.ora_move_bodies(self._h)
+
+    def open_boundaries(self):
+        self._lib.ora_open_boundaries(self._h)
 
     def record_moments(self):
         self._lib.ora_record_moments(self._h)

@@ -21,7 +21,9 @@
  *      Eqs. 37-38 without the internal-mass terms).
  *   2. One more interpolation gives the final no-slip residual r^N.
  *   3. Free bodies: Newton-Euler update in FP64 (Eqs. 37-42).
- *   4. Moments of the corrected state (Eq. 7) are recorded; collision with
+ *   4. Extrapolation boundary columns are rebuilt from their inner neighbours
+ *      (ora_open_boundaries).  Moments of the corrected state (Eq. 7) are
+ *      recorded; collision with
  *      the equilibrium of Eq. 3: BGK (Eq. 1 with the single-relaxation
  *      operator named in section 2.1) or the MRT operator of Eqs. 2, 5, 6.
  *   5. Streaming (Eq. 1) with the domain boundary rules.
@@ -56,7 +58,8 @@ static const double ora_w[ORA_Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                                     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
 enum { ORA_PERIODIC = 0, ORA_BOUNCEBACK = 1, ORA_FREESLIP = 2,
-       ORA_INLET_EQ = 3, ORA_OUTLET_ZEROGRAD = 4 };
+       ORA_INLET_EQ = 3, ORA_OUTLET_ZEROGRAD = 4, ORA_INLET_NEE = 5,
+       ORA_OUTLET_NEE = 6 };
 enum { ORA_BODY_FIXED = 0, ORA_BODY_PRESCRIBED = 1, ORA_BODY_FREE = 2 };
 
 typedef struct {
@@ -557,7 +560,38 @@ void ora_move_bodies(ora_lattice *L) {
 
 /* ---------------------------------------------------------------- LBM */
 
-static int is_open(int bc) { return bc == ORA_INLET_EQ || bc == ORA_OUTLET_ZEROGRAD; }
+static int is_open(int bc) {
+  return bc == ORA_INLET_EQ || bc == ORA_OUTLET_ZEROGRAD || bc == ORA_INLET_NEE ||
+         bc == ORA_OUTLET_NEE;
+}
+
+/* Non-equilibrium extrapolation (the velocity and pressure boundary scheme
+ * the paper uses at the inlet and outlet of section 3.2): the whole
+ * post-stream state of a boundary node x_b is rebuilt from its inner
+ * neighbour x_f as
+ *     f_i(x_b) = f_i^eq(rho_b, u_b) + [f_i(x_f) - f_i^eq(rho(x_f), u(x_f))].
+ * Inlet (-x side, column 0 from column 1): u_b = U_in, rho_b = rho(x_f).
+ * Outlet (+x side, column nx-1 from column nx-2): rho_b = rho0,
+ * u_b = u(x_f).  The rebuilt node then collides and streams like any other;
+ * populations it would receive from outside are never read. */
+void ora_open_boundaries(ora_lattice *L) {
+  int nx = L->nx;
+  for (int side = 0; side < 2; ++side) {
+    if (L->bc[side] != (side == 0 ? ORA_INLET_NEE : ORA_OUTLET_NEE)) continue;
+    int xb = side == 0 ? 0 : nx - 1, xf = side == 0 ? 1 : nx - 2;
+    for (int y = 0; y < L->ny; ++y) {
+      double p[ORA_Q], rho, jx, jy, fe_f[ORA_Q], fe_b[ORA_Q];
+      node_pops(L, L->f, xf, y, p);
+      ora_moments(p, &rho, &jx, &jy);
+      ora_feq(rho, jx / rho, jy / rho, fe_f);
+      if (side == 0)
+        ora_feq(rho, L->inlet_u[0], L->inlet_u[1], fe_b);
+      else
+        ora_feq(L->rho0, jx / rho, jy / rho, fe_b);
+      for (int i = 0; i < ORA_Q; ++i) L->f[idx(L, i, xb, y)] = fe_b[i] + (p[i] - fe_f[i]);
+    }
+  }
+}
 
 static int find_dir(int ex, int ey) {
   for (int i = 0; i < ORA_Q; ++i)
@@ -598,7 +632,10 @@ void ora_record_moments(ora_lattice *L) {
  *   free-slip: specular reflection of the normal component;
  *   inlet (-x side): the first column is held at f^eq(rho0, U_in);
  *   outlet (+x side): the populations entering from outside are copied from
- *     column nx-2.  Populations leaving through an open side are dropped. */
+ *     column nx-2;
+ *   extrapolation sides: nothing here (ora_open_boundaries rebuilds the
+ *     boundary column before the collision).
+ * Populations leaving through an open side are dropped. */
 void ora_collide_stream(ora_lattice *L) {
   int nx = L->nx, ny = L->ny;
   size_t n = (size_t)nx * ny;
@@ -659,6 +696,7 @@ void ora_step(ora_lattice *L, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     ora_ib_correct(L);
     ora_move_bodies(L);
+    ora_open_boundaries(L);
     ora_record_moments(L);
     ora_collide_stream(L);
     L->steps++;

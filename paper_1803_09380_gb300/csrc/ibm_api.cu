@@ -345,15 +345,19 @@ ibm_status ibm::create_lattice(const ibm_lattice_desc* desc, ibm_handle* out, cu
   if (!is_finite(d.rho0) || d.rho0 <= 0.0) return fail(nullptr, IBM_ERR_INVALID, "rho0 must be finite and > 0");
   if (d.prec < 0 || d.prec > 3) return fail(nullptr, IBM_ERR_INVALID, "unknown precision");
   for (int s = 0; s < 4; ++s) {
-    if (d.bc[s] < 0 || d.bc[s] > 4) return fail(nullptr, IBM_ERR_INVALID, "unknown boundary rule");
+    if (d.bc[s] < 0 || d.bc[s] > 6) return fail(nullptr, IBM_ERR_INVALID, "unknown boundary rule");
     if (!is_finite(d.wall_u[s][0]) || !is_finite(d.wall_u[s][1]))
       return fail(nullptr, IBM_ERR_INVALID, "wall velocity not finite");
   }
   if ((d.bc[0] == IBM_BC_PERIODIC) != (d.bc[1] == IBM_BC_PERIODIC) ||
       (d.bc[2] == IBM_BC_PERIODIC) != (d.bc[3] == IBM_BC_PERIODIC))
     return fail(nullptr, IBM_ERR_INVALID, "periodic sides must be paired");
-  if (d.bc[1] == IBM_BC_INLET_EQ || d.bc[2] == IBM_BC_INLET_EQ || d.bc[3] == IBM_BC_INLET_EQ)
-    return fail(nullptr, IBM_ERR_INVALID, "inlet supported on the -x side only");
+  for (int s = 1; s < 4; ++s)
+    if (d.bc[s] == IBM_BC_INLET_EQ || d.bc[s] == IBM_BC_INLET_NEE)
+      return fail(nullptr, IBM_ERR_INVALID, "inlet supported on the -x side only");
+  for (int s = 0; s < 4; ++s)
+    if (s != 1 && d.bc[s] == IBM_BC_OUTLET_NEE)
+      return fail(nullptr, IBM_ERR_INVALID, "outlet supported on the +x side only");
   if (d.bc[0] == IBM_BC_OUTLET_ZEROGRAD || d.bc[2] == IBM_BC_OUTLET_ZEROGRAD ||
       d.bc[3] == IBM_BC_OUTLET_ZEROGRAD)
     return fail(nullptr, IBM_ERR_INVALID, "outlet supported on the +x side only");
@@ -504,13 +508,14 @@ ibm_status ibm_add_markers(ibm_handle h, const double* xy, const double* ds, int
       for (int k = 0; k < n; ++k) mds[k] = per / n;
     }
     // The 4 x 4 support of every marker must stay inside closed axes and off
-    // the inlet / outlet columns.
+    // the inlet / outlet columns (and off the inner neighbour of an
+    // extrapolation side, which rebuilds the boundary column).
     const Geom& g = c.geom;
     for (int k = 0; k < n; ++k) {
       const long long bx = (long long)std::floor(xy[2 * k]) - 1, by = (long long)std::floor(xy[2 * k + 1]) - 1;
       if (g.bc[0] != BC_PERIODIC) {
-        const long long lo = g.bc[0] == BC_INLET ? 1 : 0;
-        const long long hi = g.bc[1] == BC_OUTLET ? g.nx - 3 : g.nx - 1;
+        const long long lo = g.bc[0] == BC_INLET ? 1 : (g.bc[0] == BC_INLET_NEE ? 2 : 0);
+        const long long hi = g.bc[1] == BC_OUTLET ? g.nx - 3 : (g.bc[1] == BC_OUTLET_NEE ? g.nx - 3 : g.nx - 1);
         if (bx < lo || bx + 3 > hi)
           return fail(h, IBM_ERR_INVALID, "a marker support leaves the domain or touches an inlet/outlet column");
       }

@@ -26,7 +26,8 @@
 namespace ibm {
 
 enum { PREC_FP64 = 0, PREC_FP32 = 1, PREC_FP16_DEV = 2, PREC_BF16_DEV = 3 };
-enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1, BC_FREESLIP = 2, BC_INLET = 3, BC_OUTLET = 4 };
+enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1, BC_FREESLIP = 2, BC_INLET = 3, BC_OUTLET = 4,
+       BC_INLET_NEE = 5, BC_OUTLET_NEE = 6 };
 
 // Stencil slots per marker (4 x 4 support of the delta function, Eq. 15c)
 // and capacity of the per-band-node list of covering markers.
@@ -114,7 +115,18 @@ struct StepConsts {
   R inlet_u[2];
 };
 
-__device__ __forceinline__ bool is_open(int b) { return b == BC_INLET || b == BC_OUTLET; }
+__device__ __forceinline__ bool is_open(int b) {
+  return b == BC_INLET || b == BC_OUTLET || b == BC_INLET_NEE || b == BC_OUTLET_NEE;
+}
+
+// Columns of an extrapolation side and their inner neighbours: streamed by
+// k_open_columns, one thread per row and side, never by the other kernels.
+__host__ __device__ __forceinline__ bool nee_column(const Geom& g, int x) {
+  return (g.bc[0] == BC_INLET_NEE && x <= 1) || (g.bc[1] == BC_OUTLET_NEE && x >= g.nx - 2);
+}
+__host__ __device__ __forceinline__ bool has_nee(const Geom& g) {
+  return g.bc[0] == BC_INLET_NEE || g.bc[1] == BC_OUTLET_NEE;
+}
 
 __device__ __forceinline__ long long slot_index(const Geom& g, int k, int x, int y) {
   return (long long)k * g.plane + (long long)y * g.nxp + x;
@@ -189,7 +201,7 @@ __device__ __forceinline__ OddTargets oddTargets(const Geom& g, int x, int y, in
 // two share slots and must be handled by one thread, reads before writes).
 __device__ __forceinline__ bool needs_boundary_path(const Geom& g, int x, int y) {
   return (g.bc[0] != BC_PERIODIC && x == 0) ||
-         (g.bc[1] != BC_PERIODIC && x >= g.nx - (g.bc[1] == BC_OUTLET ? 2 : 1)) ||
+         (g.bc[1] != BC_PERIODIC && x >= g.nx - ((g.bc[1] == BC_OUTLET || g.bc[1] == BC_OUTLET_NEE) ? 2 : 1)) ||
          (g.bc[2] != BC_PERIODIC && y == 0) ||
          (g.bc[3] != BC_PERIODIC && y == g.ny - 1);
 }

@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(256) k_band_collide(IbArgs<P> a) {
   for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / kSegW; k < nseg; k += nw) {
     const int seg = a.seglist[k];
     const int y = seg / nseg_x, x = (seg % nseg_x) * kSegW + lane;
-    if (x >= g.nx) continue;
+    if (x >= g.nx || nee_column(g, x)) continue;          // k_open_columns streams those
     // Eq. 27 at a band node first (the same thread then reads the node's
     // corrected populations; they are its own slots)
     if (!a.apply && a.N > 0) {

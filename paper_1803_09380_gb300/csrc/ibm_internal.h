@@ -150,6 +150,7 @@ namespace ibm {
 // Number of CUDA kernels one time step launches (matches enqueue_step).
 inline int kernels_per_step(const Ctx& h) {
   int k = 1;                                       // collide + stream
+  if (has_nee(h.geom)) k += 1;                     // extrapolation columns
   if (h.nm > 0) {
     const int N = h.desc.n_corr;
     (void)N;

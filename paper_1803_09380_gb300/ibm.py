@@ -26,6 +26,7 @@ IBM_OK, IBM_ERR_INVALID, IBM_ERR_NOMEM, IBM_ERR_CUDA = 0, 1, 2, 3
 IBM_ERR_BOUNDS, IBM_ERR_DIVERGED, IBM_ERR_TIMEOUT, IBM_WARN_NOT_CONVERGED = 4, 5, 6, 7
 IBM_FP64, IBM_FP32, IBM_FP16_DEV, IBM_BF16_DEV = 0, 1, 2, 3
 PERIODIC, BOUNCEBACK, FREESLIP, INLET_EQ, OUTLET_ZEROGRAD = 0, 1, 2, 3, 4
+INLET_NEE, OUTLET_NEE = 5, 6   # non-equilibrium extrapolation inlet / outlet
 BODY_FIXED, BODY_PRESCRIBED, BODY_FREE = 0, 1, 2
 COLL_BGK, COLL_MRT = 0, 1
 PAPER_MRT_RATES = (1.1, 1.25, 1.8)   # s_e, s_eps, s_q of section 3

@@ -22,6 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 PERIODIC, BOUNCEBACK, FREESLIP, INLET_EQ, OUTLET_ZEROGRAD = 0, 1, 2, 3, 4
+INLET_NEE, OUTLET_NEE = 5, 6   # non-equilibrium extrapolation sides
 BODY_FIXED, BODY_PRESCRIBED, BODY_FREE = 0, 1, 2
 
 
