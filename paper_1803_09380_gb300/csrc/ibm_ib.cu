@@ -354,16 +354,22 @@ __device__ __forceinline__ void grid_barrier(unsigned long long* bar, int* ctr, 
     return;
   }
   if (threadIdx.x == 0) {
-    __threadfence();
+    // The arrival is a release at GPU scope (it carries the CTA's writes,
+    // ordered before it by the block barrier above); the polling loads are
+    // acquires, so the other CTAs' writes are visible once the count is
+    // reached (the block barrier below hands them to the CTA's threads).
     const unsigned long long g = gridDim.x;
-    const unsigned long long t = atomicAdd(bar, 1ull) + 1ull;
+    unsigned long long t;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(t) : "l"(bar) : "memory");
+    t += 1ull;
     const unsigned long long target = ((t + g - 1) / g) * g;
-    volatile unsigned long long* v = bar;
     const long long t0 = clock64();
-    while (*v < target) {
+    unsigned long long cur;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(bar) : "memory");
+      if (cur >= target) break;
       if (clock64() - t0 > kBarrierCycles) { atomicOr(&ctr[CTR_ERR], ERR_BARRIER); break; }
     }
-    __threadfence();
   }
   __syncthreads();
 }

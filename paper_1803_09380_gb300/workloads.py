@@ -121,6 +121,48 @@ def couette_analytic(case: Case, x: np.ndarray, y: np.ndarray):
     return ut * sx, ut * sy
 
 
+def paper_cylinder(re: float, diameter: int = 40, u0: float = 0.1, mrt: bool = True,
+                   n_corr: int = 10) -> Case:
+    """Flow past a fixed cylinder as section 3.2 sets it up: a 40D x 20D
+    channel, the cylinder at (10D, 10D), D = 40 lattice units, inflow
+    U0 = 0.1 through a non-equilibrium-extrapolation inlet, a free outflow
+    through an extrapolation outlet, free-slip side walls (the paper does
+    not say), the MRT rates of section 3 and tau from Re = U0 D / nu."""
+    nu = u0 * diameter / re
+    tau = 0.5 + 3.0 * nu
+    c = (10.0 * diameter, 10.0 * diameter + 0.3)
+    markers = int(round(math.pi * diameter))
+    xy, ds = ring(c[0], c[1], diameter / 2.0, count=markers)
+    body = Body(xy, ds, BODY_FIXED, xc=c, radius=diameter / 2.0)
+    return Case(f"cylinder_re{re:g}_d{diameter}", 40 * diameter, 20 * diameter, tau,
+                bc=(INLET_NEE, OUTLET_NEE, FREESLIP, FREESLIP), inlet_u=(u0, 0.0), n_corr=n_corr,
+                bodies=[body], mrt=(1.1, 1.25, 1.8) if mrt else None,
+                meta=dict(diameter=diameter, u_in=u0, re=re))
+
+
+def paper_settling(density_ratio: float, diameter: int = 26, tau: float = 0.6,
+                   drop: float = 3.0) -> Case:
+    """One particle settling in a channel (section 3.3.1), laid along x: the
+    channel is 4D wide (bounce-back walls at the y sides) and 400/13 D long,
+    the particle (D = 0.1 cm on 26 lattice units) starts 0.31 W off the
+    centre line, `drop` diameters below the zero-velocity inlet at -x, and
+    falls toward the free outlet at +x.  Fluid: 1 g/cm^3, nu = 0.01 cm^2/s,
+    |g| = 980 cm/s^2, tau = 0.6; the lattice spacing and time step follow
+    from D and tau, which fix g in lattice units."""
+    d_phys, nu_phys, g_phys = 0.1, 0.01, 980.0
+    dx = d_phys / diameter
+    nu = (tau - 0.5) / 3.0
+    dt = nu * dx * dx / nu_phys
+    g = g_phys * dt * dt / dx
+    width = 4 * diameter
+    length = int(round(400.0 / 13.0 * diameter))
+    b = disk(drop * diameter, width / 2.0 + 0.31 * width, float(diameter), density_ratio, g)
+    b.gravity = (g, 0.0)
+    return Case(f"settle_channel_{density_ratio:g}", length, width, tau,
+                bc=(INLET_NEE, OUTLET_NEE, BOUNCEBACK, BOUNCEBACK), inlet_u=(0.0, 0.0), bodies=[b],
+                meta=dict(diameter=diameter, dx_cm=dx, dt_s=dt, g=g, width=width))
+
+
 def taylor_green(L: int, re: float = 10.0, tau: float = 0.65, n_corr: int = 10,
                  markers: int | None = None) -> Case:
     """Taylor-Green vortices with an artificial cylinder (section 3.1.1): a
