@@ -1,0 +1,87 @@
+"""The paper's flow past a fixed cylinder (section 3.2) run on the CUDA
+library and compared with the values the paper prints for its own method
+(Table 1, row 'Present'; tests/golden/cylinder_table1.json).
+
+Setup as section 3.2 states it (workloads.paper_cylinder): 40D x 20D, D =
+40, U0 = 0.1, extrapolation inlet and outlet, MRT with the rates of section
+3, FP32.  Readings where the paper is silent: free-slip side walls, uniform
+flow as the initial state, coefficients from the Eq. 29 force on the body,
+C = F / (rho0 U0^2 D / 2), Strouhal number from the lift period.  The paper
+gives no error bars; the tolerances are what an independent implementation
+of the same scheme can be expected to meet (a few per cent on forces, one
+on the shedding frequency)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1803_09380_gb300 import ibm
+from paper_1803_09380_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _table():
+    with open(os.path.join(HERE, "golden", "cylinder_table1.json")) as f:
+        return json.load(f)
+
+
+def _run(re, steps, every=20):
+    case = wl.paper_cylinder(re)
+    lat = ibm.Lattice.from_case(case, prec="fp32")
+    shp = (case.ny, case.nx)
+    lat.init_equilibrium(np.ones(shp), np.full(shp, case.inlet_u[0]), np.zeros(shp))
+    q = 0.5 * case.rho0 * case.inlet_u[0] ** 2 * case.meta["diameter"]
+    hist = []
+    for _ in range(steps // every):
+        lat.step(every, flags=ibm.STEP_NO_MACRO)
+        b = lat.bodies[0]
+        hist.append((b[6] / q, b[7] / q))
+    return case, lat, np.array(hist)
+
+
+def _wake_length(case, ux):
+    """Recirculation length behind the cylinder over D: from the rear
+    surface to where u_x on the centre line turns positive again after its
+    minimum (centre line between the two node rows around y_c)."""
+    D = case.meta["diameter"]
+    xc, yc = case.bodies[0].xc
+    row = 0.5 * (ux[int(math.floor(yc)), :] + ux[int(math.floor(yc)) + 1, :])
+    xr = xc + D / 2.0
+    lo = int(math.ceil(xr))
+    win = row[lo:lo + 5 * D]
+    k = int(np.argmin(win))
+    assert win[k] < 0                                       # there is a recirculation bubble
+    j = k + int(np.argmax(win[k:] >= 0))
+    xz = lo + (j - 1) + win[j - 1] / (win[j - 1] - win[j])
+    return (xz - xr) / D
+
+
+def test_steady_drag_and_wake_at_re20():
+    case, lat, h = _run(20, 60000)
+    cd = h[len(h) // 2:, 0].mean()
+    want = _table()["Re20"]
+    assert abs(cd / want["Cd"] - 1) < 0.05, (cd, want)
+    assert np.abs(h[len(h) // 2:, 1]).max() < 0.01          # no lift in the steady wake
+    lat.step(1)
+    _, ux, _ = lat.moments()
+    lw = _wake_length(case, ux)
+    assert abs(lw / want["Lw_over_D"] - 1) < 0.10, (lw, want)
+
+
+def test_vortex_shedding_at_re100():
+    case, _, h = _run(100, 160000)
+    tail = h[len(h) // 2:]
+    cd = tail[:, 0].mean()
+    cl = (tail[:, 1].max() - tail[:, 1].min()) / 2
+    c = tail[:, 1] - tail[:, 1].mean()
+    up = np.where(np.diff(np.sign(c)) > 0)[0]
+    period = (up[-1] - up[0]) / (len(up) - 1) * 20
+    st = case.meta["diameter"] / (period * case.inlet_u[0])
+    want = _table()["Re100"]
+    assert abs(cd / want["Cd"] - 1) < 0.05, (cd, want)
+    assert abs(cl / want["Cl"] - 1) < 0.10, (cl, want)
+    assert abs(st / want["St"] - 1) < 0.03, (st, want)
