@@ -62,8 +62,10 @@ __host__ __device__ constexpr R wgt(int i) {
 // 16-bit forms keep f_i - w_i (the deviation from the rest weight).
 template <int P> struct Prec;
 // ld/st convert between storage and the full population f_i; ldv/stv are
-// the vector kernels' forms, which keep the stored variable (kDev: the
-// deviation f_i - w_i for 16-bit storage, f_i otherwise).
+// the vector kernels' forms, which hand the collision the deviation
+// f_i - w_i where kDev is set (16-bit storage keeps the deviation itself;
+// FP32 stores f_i and converts, which keeps the velocity terms' low bits)
+// and f_i otherwise.
 template <> struct Prec<PREC_FP64> {
   typedef double S; typedef double R;
   static constexpr bool kDev = false;
@@ -74,11 +76,11 @@ template <> struct Prec<PREC_FP64> {
 };
 template <> struct Prec<PREC_FP32> {
   typedef float S; typedef float R;
-  static constexpr bool kDev = false;
+  static constexpr bool kDev = true;      // collide deviations, store full f
   static __device__ __forceinline__ R ld(S v, int) { return v; }
   static __device__ __forceinline__ S st(R v, int) { return v; }
-  static __device__ __forceinline__ R ldv(S v, int) { return v; }
-  static __device__ __forceinline__ S stv(R v, int) { return v; }
+  static __device__ __forceinline__ R ldv(S v, int i) { return v - wgt<float>(i); }
+  static __device__ __forceinline__ S stv(R v, int i) { return v + wgt<float>(i); }
 };
 template <> struct Prec<PREC_FP16_DEV> {
   typedef __half S; typedef float R;

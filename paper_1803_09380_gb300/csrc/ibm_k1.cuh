@@ -9,6 +9,31 @@
 
 namespace ibm {
 
+// The nine equilibria of Eq. 3 in the moment form of feq_i, evaluated by
+// opposite pairs: f_i and f_opp(i) share w_i [lead - 1.5 tr Pi + 4.5 ee:Pi]
+// and differ in the sign of 3 w_i e.j, so a pair costs a few operations
+// instead of two full evaluations.
+template <class R>
+__device__ __forceinline__ void feq_all(R lead, R jx, R jy, R pxx, R pxy, R pyy, R* fe) {
+  const R tr = pxx + pyy;
+  const R base = lead - R(1.5) * tr;
+  const R w0 = R(4) / R(9), w1 = R(1) / R(9), w5 = R(1) / R(36);
+  fe[0] = w0 * base;
+  const R ax = w1 * (base + R(4.5) * pxx), bx = (R(3) * w1) * jx;
+  fe[1] = ax + bx;
+  fe[3] = ax - bx;
+  const R ay = w1 * (base + R(4.5) * pyy), by = (R(3) * w1) * jy;
+  fe[2] = ay + by;
+  fe[4] = ay - by;
+  const R q = R(4.5) * tr, c = R(9) * pxy;      // ee:Pi = tr +- 2 pxy on the diagonals
+  const R ad = w5 * (base + q + c), bd = (R(3) * w5) * (jx + jy);
+  fe[5] = ad + bd;
+  fe[7] = ad - bd;
+  const R ae = w5 * (base + q - c), be = (R(3) * w5) * (jy - jx);
+  fe[6] = ae + be;
+  fe[8] = ae - be;
+}
+
 // DEV: p holds deviations d_i = f_i - w_i (the 16-bit storage form) and so
 // does ps.  Since sum_i w_i = 1 and sum_i e_i w_i = 0, the deviations' sums
 // are rho - 1 and j, and f_i^eq - w_i is the equilibrium of Eq. 3 with rho
@@ -23,11 +48,10 @@ __device__ __forceinline__ void bgk(const R* p, R* ps, R& rho, R& jx, R& jy, R o
   R inv = R(1) / rho;
   R ux = jx * inv, uy = jy * inv;
   R pxx = jx * ux, pxy = jx * uy, pyy = jy * uy;
+  R fe[9];
+  feq_all<R>(lead, jx, jy, pxx, pxy, pyy, fe);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    R fe = feq_i<R>(i, lead, jx, jy, pxx, pxy, pyy);
-    ps[i] = p[i] - omega * (p[i] - fe);
-  }
+  for (int i = 0; i < 9; ++i) ps[i] = p[i] - omega * (p[i] - fe[i]);
 }
 
 // MRT (Eq. 2) written as BGK at the stress rate s_nu = 1/tau plus the
@@ -47,8 +71,9 @@ __device__ __forceinline__ void mrt(const R* p, R* ps, R& rho, R& jx, R& jy,
   R ux = jx * inv, uy = jy * inv;
   R pxx = jx * ux, pxy = jx * uy, pyy = jy * uy;
   R d[9];
+  feq_all<R>(lead, jx, jy, pxx, pxy, pyy, d);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) d[i] = p[i] - feq_i<R>(i, lead, jx, jy, pxx, pxy, pyy);
+  for (int i = 0; i < 9; ++i) d[i] = p[i] - d[i];
   const R s14 = (d[1] + d[3]) + (d[2] + d[4]);
   const R s58 = (d[5] + d[7]) + (d[6] + d[8]);
   const R me = c.mrt_k[0] * ((s58 + s58) - s14 - R(4) * d[0]);
@@ -81,6 +106,29 @@ __device__ __forceinline__ void collide(const R* p, R* ps, R& rho, R& jx, R& jy,
     bgk<R, DEV>(p, ps, rho, jx, jy, c.omega);
 }
 
+// Collision of full populations p (the scalar paths).  Where the storage
+// precision collides deviations (Prec<P>::kDev), p - w_i is formed first
+// (exact in FP32 while f_i stays within a factor two of w_i) and the weights
+// are added back once: the velocity terms are then added to rho - 1, not to
+// rho ~ 1, which keeps their low bits in single precision.
+template <int P, bool MRT>
+__device__ __forceinline__ void collide_full(const typename Prec<P>::R* p, typename Prec<P>::R* ps,
+                                             typename Prec<P>::R& rho, typename Prec<P>::R& jx,
+                                             typename Prec<P>::R& jy,
+                                             const StepConsts<typename Prec<P>::R>& c) {
+  typedef typename Prec<P>::R R;
+  if constexpr (Prec<P>::kDev) {
+    R d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = p[i] - wgt<R>(i);
+    collide<R, MRT, true>(d, ps, rho, jx, jy, c);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ps[i] += wgt<R>(i);
+  } else {
+    collide<R, MRT, false>(p, ps, rho, jx, jy, c);
+  }
+}
+
 template <class R>
 __device__ __forceinline__ void write_macro(R* mac, long long n, long long k, R rho, R jx, R jy) {
   R inv = R(1) / rho;
@@ -105,7 +153,7 @@ __device__ __forceinline__ void even_node(const Geom& g, const StepConsts<typena
     for (int i = 0; i < 9; ++i) ps[i] = c.feq_in[i];
     rho = c.rho0; jx = c.rho0 * c.inlet_u[0]; jy = c.rho0 * c.inlet_u[1];
   } else {
-    collide<R, MRT>(p, ps, rho, jx, jy, c);
+    collide_full<P, MRT>(p, ps, rho, jx, jy, c);
   }
   if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x, rho, jx, jy);
 #pragma unroll
@@ -133,7 +181,7 @@ __device__ void odd_boundary(const Geom& g, const StepConsts<typename Prec<P>::R
       for (int i = 0; i < 9; ++i) ps[q][i] = c.feq_in[i];
       rho = c.rho0; jx = c.rho0 * c.inlet_u[0]; jy = c.rho0 * c.inlet_u[1];
     } else {
-      collide<R, MRT>(p, ps[q], rho, jx, jy, c);
+      collide_full<P, MRT>(p, ps[q], rho, jx, jy, c);
     }
     if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + xq, rho, jx, jy);
   }
@@ -169,7 +217,7 @@ __device__ __forceinline__ void odd_node(const Geom& g, const StepConsts<typenam
     const int sy = cy(i) > 0 ? ym : (cy(i) < 0 ? yp : y);
     p[i] = Prec<P>::ld(A[opp(i) * g.plane + (long long)sy * g.nxp + sx], opp(i));
   }
-  collide<R, MRT>(p, ps, rho, jx, jy, c);
+  collide_full<P, MRT>(p, ps, rho, jx, jy, c);
   if (MACRO) write_macro<R>(mac, (long long)g.nx * g.ny, (long long)y * g.nx + x, rho, jx, jy);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {

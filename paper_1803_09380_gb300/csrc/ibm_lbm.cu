@@ -36,8 +36,16 @@ namespace ibm {
 // through the boundary-aware path.
 constexpr int kK1Threads = 256;   // threads per collide+stream block (whole warps per row span)
 
+// Resident blocks asked of the register allocator: 4 (64 registers) for the
+// node-local even step, 3 (80) for the odd step with its shuffles; FP64
+// needs one block fewer.  Without it the allocator's own choice varied
+// with unrelated edits, once spilling the odd step's hot loop.
+constexpr int k1_min_blocks(int P, int PAR) {
+  return (PAR ? 3 : 4) - (P == PREC_FP64 ? 1 : 0);
+}
+
 template <int P, int PAR, bool MACRO, int MODE, bool MRT>
-__global__ void __launch_bounds__(kK1Threads) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
+__global__ void __launch_bounds__(kK1Threads, k1_min_blocks(P, PAR)) k_collide_stream(Geom g, StepConsts<typename Prec<P>::R> c,
                                                         typename Prec<P>::S* __restrict__ A,
                                                         typename Prec<P>::R* __restrict__ mac,
                                                         const int* __restrict__ segflag, int nseg_x) {
@@ -217,9 +225,9 @@ __global__ void k_open_columns(Geom g, StepConsts<typename Prec<P>::R> c, typena
   const long long nn = (long long)g.nx * g.ny;
   {
     R rho, jx, jy;
-    collide<R, MRT>(pb, ps[0], rho, jx, jy, c);
+    collide_full<P, MRT>(pb, ps[0], rho, jx, jy, c);
     if (MACRO) write_macro<R>(mac, nn, (long long)y * g.nx + xb, rho, jx, jy);
-    collide<R, MRT>(pf, ps[1], rho, jx, jy, c);
+    collide_full<P, MRT>(pf, ps[1], rho, jx, jy, c);
     if (MACRO) write_macro<R>(mac, nn, (long long)y * g.nx + xf, rho, jx, jy);
   }
   for (int q = 0; q < 2; ++q) {
