@@ -211,8 +211,9 @@ def run_reference(args, rank, world):
 # sources the capture ran; the figure is reported only while the sources
 # still hash to that value.  Sources: the summaries under profiles/.
 TRAFFIC = {
-    ("fp32", 4096): (1137.6e6, "94b6a1289da07c11", "profiles/k_collide_stream_fp32_couette4096.md"),
-    ("fp16", 4096): (542.7e6, "94b6a1289da07c11", "profiles/k_collide_stream_fp16_couette4096.md"),
+    ("fp32", 4096): (1139.8e6, "62a14777a1211814", "profiles/k_collide_stream_fp32_couette4096.md"),
+    ("fp16", 4096): (542.8e6, "62a14777a1211814", "profiles/k_collide_stream_fp16_couette4096.md"),
+    ("fp64", 4096): (2314.4e6, "62a14777a1211814", "profiles/k_collide_stream_fp64_couette4096.md"),
 }
 KERNEL_SOURCES = ("ibm_k1.cuh", "ibm_lbm.cu", "ibm_device.cuh")
 
@@ -304,6 +305,9 @@ def run_ours(args, rank, world, local_rank, dist):
     k1_avg_s = (k1_ms / max(k1_n, 1)) * 1e-3
     achieved = bytes_per_update * main_nodes / k1_avg_s / 1e9
     traffic, traffic_src = measured_traffic(args.prec, args.n)
+    limiter = {"fp64": "FP64 arithmetic (FP64 pipe 84 % active; profiles/k_collide_stream_fp64_couette4096.md)",
+               "fp16": "instruction issue (profiles/k_collide_stream_fp16_couette4096.md)",
+               "bf16": "instruction issue (profiles/k_collide_stream_fp16_couette4096.md)"}.get(args.prec)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": "k_collide_stream (band-free row segments, both AA step kinds)",
@@ -312,6 +316,8 @@ def run_ours(args, rank, world, local_rank, dist):
                 "avg_launch_us": k1_avg_s * 1e6, "launches_timed": k1_n,
                 "band_nodes": band_nodes, "band_segment_nodes": 32 * band_segs,
                 "step_frac": (bytes_per_update * N2 * args.steps / (ms * 1e-3) / 1e9) / peak}
+    if limiter:
+        roofline["limited_by"] = limiter
     lat.close()
 
     e2e = None
