@@ -360,7 +360,7 @@ def run_serving(args, local_rank):
                   "seed 1803"}
 
     def serve(max_active, paced):
-        with ibm.Server(device=local_rank, max_active=max_active, steps_per_launch=32) as srv:
+        with ibm.Server(device=local_rank, max_active=max_active, steps_per_launch=16) as srv:
             t0 = time.perf_counter()
             k = 0
             while k < len(stream):

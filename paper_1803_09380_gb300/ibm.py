@@ -349,7 +349,7 @@ def _scheck(st: int, srv, where: str) -> int:
     raise IBMError(st, where, msg)
 
 
-def ibm_server_create(device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=32,
+def ibm_server_create(device=0, max_device_bytes=0.0, max_active=32, steps_per_launch=16,
                       ib_cta_budget=0, ib_markers_per_cta=0):
     d = ServerDesc(int(device), float(max_device_bytes), int(max_active), int(steps_per_launch),
                    int(ib_cta_budget), int(ib_markers_per_cta))
@@ -451,7 +451,7 @@ def ibm_server_last_error(srv=None) -> str:
 class Server:
     """Owning wrapper of an ibm_server (context manager)."""
 
-    def __init__(self, device=0, max_device_bytes=0.0, max_active=16, steps_per_launch=32,
+    def __init__(self, device=0, max_device_bytes=0.0, max_active=32, steps_per_launch=16,
                  ib_cta_budget=0, ib_markers_per_cta=0):
         self.s = ibm_server_create(device, max_device_bytes, max_active, steps_per_launch, ib_cta_budget,
                                    ib_markers_per_cta)
