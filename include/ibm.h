@@ -230,9 +230,11 @@ enum {
 };
 
 /* Sets a tuning option of h (takes effect at the next step).  Concurrency
- * note: the correction kernel of a lattice with more than one CTA holds all
- * its CTAs resident while it runs; step at most two such lattices at once
- * on one GPU (the server below enforces a budget). */
+ * note: a correction kernel of more than 16 CTAs (the default for more than
+ * 512 markers) waits at a grid barrier in global memory and needs all its
+ * CTAs resident at once; step at most two such lattices at once on one GPU
+ * (the server below keeps a budget).  Grids of 2..16 CTAs run as one
+ * thread-block cluster, which the hardware schedules as a whole. */
 ibm_status ibm_set_option(ibm_handle h, int option, long long value);
 
 /* Frees every device and host resource of h (NULL is a no-op). */
@@ -267,10 +269,13 @@ typedef struct {
   double max_device_bytes;    /* budget for resident cases; <= 0: 80% of free memory */
   int max_active;             /* resident cases at once (slots), >= 1 */
   int steps_per_launch;       /* steps enqueued per case per round, >= 1 */
-  int ib_cta_budget;          /* sum of correction-kernel CTAs of resident cases; <= 0: 2 per SM */
+  int ib_cta_budget;          /* sum of the CTAs of resident cases whose correction
+                                 kernel waits at a global-memory grid barrier (a
+                                 grid the device cannot schedule as one cluster);
+                                 <= 0: 2 per SM */
   int ib_markers_per_cta;     /* a case with M markers runs its correction loop on
-                                 ceil(M / this) CTAs (one CTA when M <= this, at
-                                 most one per SM); <= 0: 512 */
+                                 ceil(M / this) CTAs, at most 16 (one thread-block
+                                 cluster; one CTA when M <= this); <= 0: 512 */
 } ibm_server_desc;
 
 enum { IBM_OUT_MACRO = 1, IBM_OUT_BODIES = 2, IBM_OUT_RESIDUAL = 4 };
