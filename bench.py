@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--ib-ctas", type=int, default=0,
                    help="CTAs of the correction kernel (0: the library's choice)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the library's default correction grid instead of timing candidates")
     p.add_argument("--ib-threads", type=int, default=0,
                    help="threads per correction-kernel CTA (0: the library's choice)")
     p.add_argument("--serve-requests", type=int, default=64)
@@ -262,8 +264,14 @@ def run_ours(args, rank, world, local_rank, dist):
     case = wl.couette(args.n, n_corr=args.n_corr)
     N2 = case.nx * case.ny
     lat = ibm.Lattice.from_case(case, prec=args.prec, device=local_rank)
+    tuned = None
     if args.ib_ctas:
         lat.set_ib_ctas(args.ib_ctas)
+    elif not args.no_autotune:
+        # the library's measured choice of the correction grid (its runs are
+        # real steps and count as warm-up)
+        sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        tuned = lat.autotune_ib([sms * k // 8 for k in (4, 5, 6, 7, 8)], steps_each=50)
     if args.ib_threads:
         lat.set_ib_threads(args.ib_threads)
     stream = lat._stream
@@ -337,7 +345,9 @@ def run_ours(args, rank, world, local_rank, dist):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": DTYPE[args.prec], "data": "synthetic",
-                "config": workload_config(args, case), "roofline": roofline, "cpu_baseline": cpu,
+                "config": dict(workload_config(args, case),
+                               correction_ctas=tuned[0] if tuned else (args.ib_ctas or "library default")),
+                "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "serving": serving}
         print(json.dumps(line), flush=True)
 

@@ -229,6 +229,19 @@ enum {
   IBM_OPT_IB_THREADS = 2 /* threads per correction-kernel CTA: 256 (default), 512 or 1024 */
 };
 
+/* Chooses the correction kernel's CTA count by measurement: for each of the
+ * n candidates (CTA counts as for IBM_OPT_IB_CTAS; NULL or n == 0: a default
+ * set around the SM count) the lattice takes steps_each ordinary time steps,
+ * timed with CUDA events on its stream; the fastest count is then set and
+ * written to *best (optional), its time per step to *best_us (optional).
+ * The steps are real steps of the simulation (n * steps_each of them;
+ * results do not depend on the CTA count, so the trajectory is the one any
+ * single setting would give).  Synchronises the lattice's stream.  No
+ * counterpart in the paper: it is a deployment aid.  Errors: IBM_ERR_INVALID
+ * for steps_each < 2 or a negative candidate. */
+ibm_status ibm_autotune_ib(ibm_handle h, const int *candidates, int n, int steps_each, int *best,
+                           double *best_us);
+
 /* Sets a tuning option of h (takes effect at the next step).  Concurrency
  * note: a correction kernel of more than 16 CTAs (the default for more than
  * 512 markers) waits at a grid barrier in global memory and needs all its

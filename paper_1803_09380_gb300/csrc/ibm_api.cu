@@ -2,6 +2,7 @@
 // allocation, the per-step launch sequence and its CUDA-graph replay, and
 // field transfers.  Every entry point catches C++ exceptions and returns a
 // status; none lets one cross the ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -193,6 +194,14 @@ void choose_ib_grid(Ctx& c) {
   c.ib_grid = c.ib_grid_opt > 0 ? (c.ib_grid_opt < c.ib_grid_max ? c.ib_grid_opt : c.ib_grid_max)
                                 : (M <= kSmallIbMarkers ? 1 : wide);
   c.ib_cluster = false;
+  // The grid barrier's arrival counter only grows and each barrier waits for
+  // the next multiple of the grid size: a new grid size must start from a
+  // counter that is a multiple of it, so it restarts at zero (every caller
+  // has the stream's earlier work ordered before this memset).
+  if (c.ib_grid != c.ib_grid_last && c.dbar) {
+    cudaMemsetAsync(c.dbar, 0, sizeof(unsigned long long), c.stream);
+    c.ib_grid_last = c.ib_grid;
+  }
   if (c.ib_grid >= 2 && c.ib_grid <= kMaxIbCluster) {
     if (c.ib_cluster_max < 0) c.ib_cluster_max = ib_max_cluster(c.prec, c.ib_threads);
     c.ib_cluster = c.ib_grid <= c.ib_cluster_max;
@@ -829,6 +838,65 @@ ibm_status ibm_get_sizes(ibm_handle h, long long* nodes, int* markers, int* bodi
     if (band_segments) *band_segments = h->nm > 0 ? ctr[CTR_NSEG] : 0;
   }
   return IBM_OK;
+}
+
+ibm_status ibm_autotune_ib(ibm_handle h, const int* candidates, int n, int steps_each, int* best,
+                           double* best_us) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  if (steps_each < 2) return fail(h, IBM_ERR_INVALID, "steps_each must be >= 2");
+  if (n < 0 || (n > 0 && !candidates)) return fail(h, IBM_ERR_INVALID, "invalid candidate list");
+  for (int k = 0; k < n; ++k)
+    if (candidates[k] < 0) return fail(h, IBM_ERR_INVALID, "negative candidate");
+  std::vector<int> cand(candidates, candidates + n);
+  if (cand.empty()) {
+    // one CTA, a cluster, and 1/2, 3/4 and all of the SMs
+    const int sms = h->ib_grid_max;
+    for (int v : {1, 8, 16, sms / 2, (3 * sms + 3) / 4, sms})
+      if (v >= 1 && std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+  }
+  if (h->nm == 0) {                      // nothing to tune: no correction kernel
+    if (best) *best = 0;
+    if (best_us) *best_us = 0.0;
+    return IBM_OK;
+  }
+  try {
+    DeviceGuard guard(h->device);
+    if (!guard.ok) return fail(h, IBM_ERR_CUDA, "cannot select the CUDA device");
+    cudaEvent_t e0, e1;
+    IBM_CK(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaGetLastError();
+      return fail(h, IBM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    int pick = cand[0];
+    float pick_ms = -1.0f;
+    ibm_status st = IBM_OK;
+    for (int v : cand) {
+      if ((st = ibm_set_option(h, IBM_OPT_IB_CTAS, v)) != IBM_OK) break;
+      // two untimed steps build both step kinds' graphs for this setting
+      if ((st = ibm_step(h, 2, IBM_STEP_NO_MACRO)) != IBM_OK) break;
+      cudaEventRecord(e0, h->stream);
+      if ((st = ibm_step(h, steps_each, IBM_STEP_NO_MACRO)) != IBM_OK) break;
+      cudaEventRecord(e1, h->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = IBM_ERR_CUDA; break; }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (pick_ms < 0.0f || ms < pick_ms) { pick_ms = ms; pick = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != IBM_OK) {
+      if (st == IBM_ERR_CUDA) { cudaGetLastError(); return fail(h, st, "timing the candidates failed"); }
+      return st;
+    }
+    if ((st = ibm_set_option(h, IBM_OPT_IB_CTAS, pick)) != IBM_OK) return st;
+    if (best) *best = pick;
+    if (best_us) *best_us = 1e3 * (double)pick_ms / steps_each;
+    return check_device_flags(h);
+  } catch (...) {
+    return fail(h, IBM_ERR_NOMEM, "host allocation failed");
+  }
 }
 
 ibm_status ibm_set_option(ibm_handle h, int option, long long value) {

@@ -114,6 +114,7 @@ struct Ctx {
   int ib_threads = kIbThreads;               // threads per correction-loop CTA: 256, 512, 1024
   bool ib_cluster = false;                   // launch the correction kernel as one cluster
   int ib_cluster_max = -1;                   // largest schedulable cluster (-1: not yet asked)
+  int ib_grid_last = 0;                      // grid size the barrier counter is aligned to
   int ib_grid_opt = 0;                       // caller's choice (IBM_OPT_IB_CTAS), 0 = by size
   bool band_collide = true;                  // stream the band segments after the correction
   bool band_valid = false;

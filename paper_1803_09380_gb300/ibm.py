@@ -46,7 +46,7 @@ SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields
            "ibm_abi_version", "ibm_ib_correct_noalloc", "ibm_set_option",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_wait",
            "ibm_server_result", "ibm_server_release", "ibm_server_get_stats", "ibm_server_destroy",
-           "ibm_server_last_error", "ibm_set_marker_velocities")
+           "ibm_server_last_error", "ibm_set_marker_velocities", "ibm_autotune_ib")
 IBM_OPT_IB_CTAS, IBM_OPT_IB_THREADS = 1, 2
 OUT_MACRO, OUT_BODIES, OUT_RESIDUAL = 1, 2, 4
 
@@ -146,6 +146,7 @@ def load(build_if_missing: bool = True):
         lib.ibm_ib_correct_noalloc.argtypes = [ci, ci, ci, vp, ci, vp, vp, vp, ci, vp, vp, vp]
         lib.ibm_set_option.argtypes = [vp, ci, ctypes.c_longlong]
         lib.ibm_set_marker_velocities.argtypes = [vp, _D, ci]
+        lib.ibm_autotune_ib.argtypes = [vp, ctypes.POINTER(ci), ci, ci, ctypes.POINTER(ci), _D]
         lib.ibm_server_create.argtypes = [ctypes.POINTER(ServerDesc), ctypes.POINTER(vp)]
         lib.ibm_server_submit.argtypes = [vp, ctypes.POINTER(CaseDesc), ctypes.POINTER(ctypes.c_longlong)]
         lib.ibm_server_progress.argtypes = [vp, ctypes.POINTER(ci)]
@@ -336,6 +337,18 @@ def ibm_set_marker_velocities(h, uv) -> None:
     uv = np.ascontiguousarray(uv, dtype=np.float64).reshape(-1, 2)
     _check(load().ibm_set_marker_velocities(h, uv.ctypes.data_as(_D), uv.shape[0]), h,
            "ibm_set_marker_velocities")
+
+
+def ibm_autotune_ib(h, candidates=None, steps_each=20):
+    """Measured choice of the correction kernel's CTA count (the candidate
+    runs are real steps); returns (best count, microseconds per step)."""
+    cand = list(candidates or [])
+    arr = (ctypes.c_int * max(len(cand), 1))(*cand)
+    best = ctypes.c_int()
+    us = ctypes.c_double()
+    _check(load().ibm_autotune_ib(h, arr, len(cand), int(steps_each), ctypes.byref(best), ctypes.byref(us)),
+           h, "ibm_autotune_ib")
+    return best.value, us.value
 
 
 def ibm_set_option(h, option: int, value: int) -> None:
@@ -590,6 +603,11 @@ class Lattice:
     def set_ib_ctas(self, n: int) -> None:
         """CTAs of the correction-loop kernel (0: the default choice)."""
         ibm_set_option(self.h, IBM_OPT_IB_CTAS, n)
+
+    def autotune_ib(self, candidates=None, steps_each=20):
+        """Pick the correction kernel's CTA count by timing candidates (the
+        candidate runs advance the simulation); returns (count, us/step)."""
+        return ibm_autotune_ib(self.h, candidates, steps_each)
 
     def set_ib_threads(self, n: int) -> None:
         """Threads per correction-loop CTA: 256, 512 or 1024."""

@@ -133,3 +133,36 @@ def test_correction_results_do_not_depend_on_cta_count(prec):
         else:
             for g, r in zip(got, ref):
                 assert np.array_equal(g, r), ctas
+
+
+def test_autotuned_correction_grid_keeps_the_trajectory():
+    """The autotuner's candidate runs are ordinary steps: after it, the
+    lattice is where the same number of steps with any fixed setting puts
+    it, bit for bit; it returns one of the candidates and a positive time."""
+    case = wl.couette(256)
+    tuned = gpu_lattice(case, "fp32")
+    cand = [1, 4, 16, 57, 76, 152]
+    best, us = tuned.autotune_ib(cand, steps_each=5)
+    assert best in cand and us > 0
+    ref = gpu_lattice(case, "fp32")
+    ref.step(len(cand) * (2 + 5))
+    tuned.step(3)
+    ref.step(3)
+    assert np.array_equal(tuned.f, ref.f) and np.array_equal(tuned.resid, ref.resid)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_changing_the_correction_grid_on_a_live_lattice(prec):
+    """Grid sizes that are not multiples of each other, switched between
+    steps of one lattice (the grid barrier's counter restarts for each new
+    size): no barrier runs out and the trajectory is bitwise that of a
+    fixed setting."""
+    case = wl.couette(256)
+    live = gpu_lattice(case, prec)
+    for ctas in (76, 95, 152, 57, 114):
+        live.set_ib_ctas(ctas)
+        live.step(3)
+    ref = gpu_lattice(case, prec)
+    ref.step(15)
+    assert np.array_equal(live.f, ref.f) and np.array_equal(live.resid, ref.resid)
+    assert np.array_equal(live.bodies, ref.bodies)
