@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define IBM_ABI_VERSION 2
+#define IBM_ABI_VERSION 3
 
 typedef struct ibm_ctx *ibm_handle; /* opaque, library-owned */
 
