@@ -622,6 +622,33 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       a.bq[8 * b + 7] = dy;
     }
   }
+  // Eq. 29: partial force and torque of each body over fixed chunks of
+  // kForceChunk markers (CTAs take chunks in turn), F_l = -ds_l A^N_l,
+  // T_l = (X_l - x_c) x F_l, FP64; the chunking does not depend on the grid,
+  // so neither do the sums.
+  const int nchunk = (M + kForceChunk - 1) / kForceChunk;
+  if (a.nb > 0) {
+    for (int k = blockIdx.x; k < nchunk; k += gridDim.x) {
+      const int lo = k * kForceChunk, hi = min(M, lo + kForceChunk);
+      const int b0 = a.mbody[lo], b1 = a.mbody[hi - 1];
+      for (int bd = b0; bd <= b1; ++bd) {
+        const BodyDev& B = a.bodies[bd];
+        const int l0 = max(lo, B.m0), l1 = min(hi, B.m1);
+        double fx = 0.0, fy = 0.0, tq = 0.0;
+        for (int l = l0 + (int)threadIdx.x; l < l1; l += blockDim.x) {
+          const double Fx = -a.ds[l] * (double)AN[2 * l], Fy = -a.ds[l] * (double)AN[2 * l + 1];
+          fx += Fx;
+          fy += Fy;
+          tq += (a.X[l] - B.xc[0]) * Fy - (a.Y[l] - B.xc[1]) * Fx;
+        }
+        block_sum3(fx, fy, tq, sh);
+        if (threadIdx.x == 0) {
+          double* o = a.fpart + ((long long)k * a.nb + bd) * 3;
+          o[0] = fx; o[1] = fy; o[2] = tq;
+        }
+      }
+    }
+  }
   grid_barrier<R>(a.bar, a.ctr, red, a.resid + N, a.cluster);
 
   // second-moment deviations summed over the iterations:
@@ -650,45 +677,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       a.Cm[3 * l + 2] = R(N) * rs * uy * uy - pyy;
     }
   }
-  if (a.apply) grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster);     // the apply reads every C_l
-
-  // Eq. 27 summed over the iterations, unless k_band_collide applies it
-  // just before it streams the band segments
-  if (N > 0 && a.apply) {
-    for (int b = tid; b < nband; b += nth) {
-      const int n = a.bnode[b];
-      apply_band_correction<P>(a.g, a.c, a.A, PAR, a.bq, a.bcnt, a.ent, a.Cm, b, n % a.g.nx, n / a.g.nx);
-    }
-  }
-
-  // Eq. 29: partial force and torque of each body over fixed chunks of
-  // kForceChunk markers (CTAs take chunks in turn), F_l = -ds_l A^N_l,
-  // T_l = (X_l - x_c) x F_l, FP64; the chunking does not depend on the grid,
-  // so neither do the sums.
-  const int nchunk = (M + kForceChunk - 1) / kForceChunk;
-  if (a.nb > 0) {
-    for (int k = blockIdx.x; k < nchunk; k += gridDim.x) {
-      const int lo = k * kForceChunk, hi = min(M, lo + kForceChunk);
-      const int b0 = a.mbody[lo], b1 = a.mbody[hi - 1];
-      for (int bd = b0; bd <= b1; ++bd) {
-        const BodyDev& B = a.bodies[bd];
-        const int l0 = max(lo, B.m0), l1 = min(hi, B.m1);
-        double fx = 0.0, fy = 0.0, tq = 0.0;
-        for (int l = l0 + (int)threadIdx.x; l < l1; l += blockDim.x) {
-          const double Fx = -a.ds[l] * (double)AN[2 * l], Fy = -a.ds[l] * (double)AN[2 * l + 1];
-          fx += Fx;
-          fy += Fy;
-          tq += (a.X[l] - B.xc[0]) * Fy - (a.Y[l] - B.xc[1]) * Fx;
-        }
-        block_sum3(fx, fy, tq, sh);
-        if (threadIdx.x == 0) {
-          double* o = a.fpart + ((long long)k * a.nb + bd) * 3;
-          o[0] = fx; o[1] = fy; o[2] = tq;
-        }
-      }
-    }
-  }
-  grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster);
 
   // body totals: one body per CTA, fixed-shape reduction over the chunks
   for (int bd = blockIdx.x; bd < a.nb; bd += gridDim.x) {
@@ -706,6 +694,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
       B.T_ib = f2;
     }
   }
+
+  if (a.apply) grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster);     // the apply reads every C_l
+
+  // Eq. 27 summed over the iterations, unless k_band_collide applies it
+  // just before it streams the band segments
+  if (N > 0 && a.apply) {
+    for (int b = tid; b < nband; b += nth) {
+      const int n = a.bnode[b];
+      apply_band_correction<P>(a.g, a.c, a.A, PAR, a.bq, a.bcnt, a.ent, a.Cm, b, n % a.g.nx, n / a.g.nx);
+    }
+  }
+
+
 }
 
 // Collide+stream of the 32-node row segments that hold band nodes, after
