@@ -327,6 +327,7 @@ def run_ours(args, rank, world, local_rank, dist):
     if limiter:
         roofline["limited_by"] = limiter
     lat.close()
+    roofline["alone"] = k1_alone(args, local_rank, peak, bytes_per_update)
 
     e2e = None
     if not args.no_e2e:
@@ -350,6 +351,28 @@ def run_ours(args, rank, world, local_rank, dist):
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "serving": serving}
         print(json.dumps(line), flush=True)
+
+
+def k1_alone(args, local_rank, peak, bytes_per_update, steps=200):
+    """The same collide+stream kernel with nothing beside it: a marker-free
+    periodic lattice of the benchmark's size and precision (every node in
+    one launch per step), kernel durations from CUDA events."""
+    from paper_1803_09380_gb300 import ibm
+    lat = ibm.Lattice(args.n, args.n, 0.8, 1.0, args.prec, device=local_rank)
+    try:
+        flags = ibm.STEP_TIME_KERNELS | ibm.STEP_NO_MACRO
+        lat.step(20, flags)
+        lat.sync()
+        lat.kernel_times()
+        lat.step(steps, flags)
+        lat.sync()
+        k_ms, k_n = lat.kernel_times()
+    finally:
+        lat.close()
+    us = 1e3 * k_ms / max(k_n, 1)
+    achieved = bytes_per_update * args.n * args.n / (us * 1e-6) / 1e9
+    return {"avg_launch_us": us, "achieved": achieved, "frac": achieved / peak, "launches_timed": k_n,
+            "what": f"k_collide_stream alone: marker-free {args.n}x{args.n} lattice, every node, {steps} steps"}
 
 
 def run_serving(args, local_rank):
