@@ -281,6 +281,25 @@ struct IbArgs {
 // Eq. 27 summed over the iterations at band node b = node (x, y):
 // f_i += w_i [3 e.dJ + 9/2 ee:dPi - 3/2 tr dPi], with dJ the final spread
 // D^N (bq[6..7]) and dPi = sum over the covering markers of W ds C_l.
+// Where the nine post-stream populations of (x, y) live: flat index (-1 for
+// an inlet node or an open side, whose value is the inlet equilibrium), the
+// slot, and the bounce-back side whose wall term is added on reading (or
+// -1) -- the rules of post_stream below, for all nine at once, so that a
+// caller can put the nine loads in flight together.
+__device__ __forceinline__ void post_stream_locs(const Geom& g, int parity, int x, int y, long long (&where)[9],
+                                                 int (&slot)[9], int (&wside)[9]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    wside[i] = -1;
+    slot[i] = i;
+    if (x == 0 && g.bc[0] == BC_INLET) { where[i] = -1; continue; }
+    if (parity == 0) { where[i] = slot_index(g, i, x, y); continue; }
+    int sx, sy;
+    if (!locE(g, x, y, i, sx, sy, slot[i], wside[i])) { where[i] = -1; continue; }
+    where[i] = slot_index(g, slot[i], sx, sy);
+  }
+}
+
 // Read-modify-write of the nine post-stream populations, by one thread.
 template <int P>
 __device__ __forceinline__ void apply_band_correction(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
@@ -316,15 +335,21 @@ __device__ __forceinline__ void apply_band_correction(const Geom& g, const StepC
     }
   }
   const R jx = bq[8 * b + 6], jy = bq[8 * b + 7];
-  long long where;
+  // the nine locations are distinct: all nine loads first, then the stores
+  long long where[9];
+  int slot[9], ws[9];
+  post_stream_locs(g, parity, x, y, where, slot, ws);
+  typename Prec<P>::S v[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (where[i] >= 0) v[i] = A[where[i]];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    post_stream<P>(g, c, A, parity, x, y, i, where);
-    if (where < 0) continue;
-    const int slot = (int)(where / g.plane);
+    if (where[i] < 0) continue;
     const R df = feq_i<R>(i, R(0), jx, jy, pxx, pxy, pyy);
-    A[where] = Prec<P>::st(Prec<P>::ld(A[where], slot) + df, slot);
+    A[where[i]] = Prec<P>::st(Prec<P>::ld(v[i], slot[i]) + df, slot[i]);
   }
+  (void)c;
 }
 
 // Grid barrier for a launch whose CTAs are all resident (one per SM).  A
@@ -476,7 +501,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
   const int rtid = nth - 1 - tid;                  // band work starts from the other end
   const int nband = min(a.ctr[CTR_NBAND], a.bcap);
   const int M = a.M, N = a.N;
-  long long where;
 
   // residual history of this step starts at zero (first read-modify-write
   // after the next barrier)
@@ -488,8 +512,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) 
     const int n = a.bnode[b];
     const int x = n % a.g.nx, y = n / a.g.nx;
     R p[9], rho, jx, jy;
+    long long w[9];
+    int sl[9], ws[9];
+    post_stream_locs(a.g, PAR, x, y, w, sl, ws);         // nine loads in flight together
+    typename Prec<P>::S v[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) p[i] = post_stream<P>(a.g, a.c, a.A, PAR, x, y, i, where);
+    for (int i = 0; i < 9; ++i)
+      if (w[i] >= 0) v[i] = a.A[w[i]];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      if (w[i] < 0) { p[i] = a.c.feq_in[i]; continue; }
+      p[i] = Prec<P>::ld(v[i], sl[i]);
+      if (ws[i] >= 0) p[i] += a.c.wall[ws[i]][i];
+    }
     moments9<R>(p, rho, jx, jy);
     a.bq[8 * b] = rho;
     a.bq[8 * b + 1] = jx;
