@@ -28,8 +28,16 @@ Parity status of the functions (what pins each one is in ``tests/``):
                                   moments, reduction to BGK at equal rates,
                                   per-moment relaxation factors 1 - s_k and
                                   the shear-wave decay set by 1/tau alone
-  Newton-Euler body update        parity unpinned beyond closed-form free
-                                  fall with no fluid force (Eqs. 40-42)
+  Newton-Euler body update        pinned by closed-form free fall with no
+                                  fluid force (Eqs. 40-42), uniform motion
+                                  without force or torque, prescribed rigid
+                                  motion (counter-clockwise for omega > 0),
+                                  Eq. 39 at contact
+  marker velocity, force, torque  pinned by the first residual of a moving
+                                  boundary in fluid at rest (= max |U_l|,
+                                  Eq. 24), mass conservation and Eulerian =
+                                  Lagrangian force (Eq. 29), and drag and
+                                  torque that oppose the motion
 """
 from __future__ import annotations
 
