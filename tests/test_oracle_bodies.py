@@ -104,3 +104,21 @@ def test_drag_opposes_translation():
     rho, ux, uy = L.moments()
     # the fluid at the boundary, inside and outside, is dragged along
     assert ux[39, 32] > 0 and ux[41, 32] > 0 and ux[23, 32] > 0 and ux[25, 32] > 0
+
+
+@pytest.mark.parametrize("rho0,u0", [(1.0, (0.03, -0.02)), (1.02, (-0.01, 0.015))])
+def test_boundary_moving_with_a_uniform_stream_needs_no_correction(rho0, u0):
+    """Galilean consistency of Eqs. 22-28: in a uniform equilibrium stream
+    (rho0, u0), a boundary whose markers move with u0 already satisfies the
+    no-slip condition.  The interpolated equilibria equal f^eq(rho0, u0)
+    and rho* = rho0 (partition of unity), so every deviation, residual,
+    force and torque vanishes and f is left as it was (to rounding)."""
+    L = oracle.Lattice(48, 48, 0.8, n_corr=10)
+    L.init_equilibrium(rho0, u0[0], u0[1])
+    f0 = L.f
+    _ring_body(L, (24.0, 23.6), 6.5, oracle.BODY_PRESCRIBED, u=u0)
+    L.ib_correct()
+    # rounding level: a wrong target or interpolation would give O(|u0|) = 1e-2
+    assert np.max(np.abs(L.resid)) < 1e-14
+    assert np.max(np.abs(L.f - f0)) < 1e-14
+    assert np.max(np.abs(L.bodies[0, 6:9])) < 1e-12
