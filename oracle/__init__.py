@@ -52,8 +52,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ibm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs: dict = {}
 
 PERIODIC, BOUNCEBACK, FREESLIP, INLET_EQ, OUTLET_ZEROGRAD = 0, 1, 2, 3, 4
 INLET_NEE, OUTLET_NEE = 5, 6
@@ -62,63 +63,99 @@ BODY_FIXED, BODY_PRESCRIBED, BODY_FREE = 0, 1, 2
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 
+_CFLAGS = ["-O2", "-ffp-contract=off", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared"]
+
+
+def _compile(path: str, extra: list, force: bool) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *_CFLAGS, *extra, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, path)
+    return path
+
 
 def build(force: bool = False) -> str:
     """Compile ibm_oracle.c into oracle/_build/liboracle.so (plain gcc, FP64,
-    no contraction into fused multiply-adds, one thread)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11",
-                           "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-o", tmp,
-                           _SRC, "-lm"])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    no contraction into fused multiply-adds, one thread), and the same source
+    with -fopenmp into liboracle_omp.so when the compiler supports it."""
+    path = _compile(_LIB_PATH, [], force)
+    try:
+        _compile(_OMP_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass                      # the threaded build is optional
+    return path
 
 
-def _load():
-    global _lib
+def _declare(lib):
+    vp = ctypes.c_void_p
+    lib.ora_delta4.restype = ctypes.c_double
+    lib.ora_delta4.argtypes = [ctypes.c_double]
+    for name in ("ora_delta2", "ora_delta3"):
+        getattr(lib, name).restype = ctypes.c_double
+        getattr(lib, name).argtypes = [ctypes.c_double]
+    lib.ora_set_delta.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.ora_set_reading.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
+    lib.ora_set_threads.restype = ctypes.c_int
+    lib.ora_set_threads.argtypes = [ctypes.c_int]
+    lib.ora_set_marker_velocities.restype = ctypes.c_int
+    lib.ora_set_marker_velocities.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
+    lib.ora_feq.argtypes = [ctypes.c_double] * 3 + [_D]
+    lib.ora_moments.argtypes = [_D, _D, _D, _D]
+    lib.ora_create.restype = vp
+    lib.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, _I, _D, _D, ctypes.c_int]
+    lib.ora_destroy.argtypes = [vp]
+    lib.ora_add_body.restype = ctypes.c_int
+    lib.ora_add_body.argtypes = [vp, ctypes.c_int, _D, _D, _D, ctypes.c_int]
+    for name in ("ora_ib_correct", "ora_move_bodies", "ora_record_moments",
+                 "ora_collide_stream", "ora_open_boundaries"):
+        getattr(lib, name).argtypes = [vp]
+    lib.ora_step.argtypes = [vp, ctypes.c_int]
+    for name in ("ora_get_f", "ora_set_f", "ora_get_resid", "ora_get_bodies",
+                 "ora_get_markers", "ora_get_force_euler"):
+        getattr(lib, name).argtypes = [vp, _D]
+    lib.ora_init_equilibrium.argtypes = [vp, _D, _D, _D]
+    lib.ora_get_moments.argtypes = [vp, _D, _D, _D]
+    lib.ora_num_markers.restype = ctypes.c_int
+    lib.ora_num_markers.argtypes = [vp]
+    lib.ora_num_bodies.restype = ctypes.c_int
+    lib.ora_num_bodies.argtypes = [vp]
+    lib.ora_set_mrt.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.ora_mrt_matrix.argtypes = [_D]
+    lib.ora_mrt_collide.argtypes = [_D, _D, _D, _D]
+
+
+def _load(threaded: bool = False):
+    """The serial library, or the -fopenmp build when ``threaded``."""
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        vp = ctypes.c_void_p
-        lib.ora_delta4.restype = ctypes.c_double
-        lib.ora_delta4.argtypes = [ctypes.c_double]
-        for name in ("ora_delta2", "ora_delta3"):
-            getattr(lib, name).restype = ctypes.c_double
-            getattr(lib, name).argtypes = [ctypes.c_double]
-        lib.ora_set_delta.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        lib.ora_set_marker_velocities.restype = ctypes.c_int
-        lib.ora_set_marker_velocities.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
-        lib.ora_feq.argtypes = [ctypes.c_double] * 3 + [_D]
-        lib.ora_moments.argtypes = [_D, _D, _D, _D]
-        lib.ora_create.restype = vp
-        lib.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                   ctypes.c_double, _I, _D, _D, ctypes.c_int]
-        lib.ora_destroy.argtypes = [vp]
-        lib.ora_add_body.restype = ctypes.c_int
-        lib.ora_add_body.argtypes = [vp, ctypes.c_int, _D, _D, _D, ctypes.c_int]
-        for name in ("ora_ib_correct", "ora_move_bodies", "ora_record_moments",
-                     "ora_collide_stream", "ora_open_boundaries"):
-            getattr(lib, name).argtypes = [vp]
-        lib.ora_step.argtypes = [vp, ctypes.c_int]
-        for name in ("ora_get_f", "ora_set_f", "ora_get_resid", "ora_get_bodies",
-                     "ora_get_markers", "ora_get_force_euler"):
-            getattr(lib, name).argtypes = [vp, _D]
-        lib.ora_init_equilibrium.argtypes = [vp, _D, _D, _D]
-        lib.ora_get_moments.argtypes = [vp, _D, _D, _D]
-        lib.ora_num_markers.restype = ctypes.c_int
-        lib.ora_num_markers.argtypes = [vp]
-        lib.ora_num_bodies.restype = ctypes.c_int
-        lib.ora_num_bodies.argtypes = [vp]
-        lib.ora_set_mrt.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
-        lib.ora_mrt_matrix.argtypes = [_D]
-        lib.ora_mrt_collide.argtypes = [_D, _D, _D, _D]
-        _lib = lib
+        key = "omp" if threaded else "serial"
+        if key in _libs:
+            return _libs[key]
+        build()
+        if threaded and not os.path.exists(_OMP_PATH):
+            raise RuntimeError("the threaded oracle build (gcc -fopenmp) is not available")
+        if threaded:
+            # idle threads sleep instead of spinning: the oracle shares the
+            # host with other work (tests, the GPU driver thread)
+            os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+        lib = ctypes.CDLL(_OMP_PATH if threaded else _LIB_PATH)
+        _declare(lib)
+        _libs[key] = lib
         return lib
+
+
+def threaded_available() -> bool:
+    build()
+    return os.path.exists(_OMP_PATH)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the threaded build (0: all host cores); returns the count
+    it will use."""
+    return int(_load(True).ora_set_threads(int(n)))
 
 
 def _dp(a: np.ndarray):
@@ -173,10 +210,20 @@ def mrt_collide(rates, p, fe) -> np.ndarray:
     return out
 
 
+# Alternative readings of section 2.3 that ora_set_reading can switch on (the
+# default, all off: nodal equilibria interpolated, rho_b = rho*, correction of
+# the post-stream populations, spreading weighted by ds).
+READINGS = ("interp_moments", "rho_b_ref", "post_collision", "unit_ds")
+
+
 class Lattice:
     """One oracle lattice: D2Q9 BGK with immersed bodies, all FP64.
     ``mrt=(s_e, s_eps, s_q)`` switches the collision to MRT (Eqs. 2, 5, 6)
     with the stress moments relaxing at 1/tau.
+
+    ``threaded`` runs the -fopenmp build (bitwise the same results; thread
+    count from ``set_threads`` or OMP_NUM_THREADS).  ``reading`` switches on
+    alternative readings of section 2.3 by name (see READINGS).
 
     ``bc`` gives the rule of the four sides (-x, +x, -y, +y); ``wall_u`` the
     velocity of each side as a moving bounce-back wall; ``inlet_u`` the inflow
@@ -184,8 +231,9 @@ class Lattice:
     """
 
     def __init__(self, nx, ny, tau, rho0=1.0, bc=(0, 0, 0, 0), wall_u=None,
-                 inlet_u=(0.0, 0.0), n_corr=10, mrt=None, delta_points=4):
-        self._lib = _load()
+                 inlet_u=(0.0, 0.0), n_corr=10, mrt=None, delta_points=4,
+                 threaded=False, reading=None):
+        self._lib = _load(threaded)
         self.nx, self.ny, self.n_corr = int(nx), int(ny), int(n_corr)
         bc_a = (ctypes.c_int * 4)(*[int(b) for b in bc])
         wu = np.zeros(8) if wall_u is None else np.ascontiguousarray(wall_u, dtype=np.float64).reshape(8)
@@ -199,6 +247,11 @@ class Lattice:
         if delta_points not in (2, 3, 4):
             raise ValueError("delta_points must be 2, 3 or 4 (Eq. 15a-c)")
         self._lib.ora_set_delta(self._h, int(delta_points))
+        if reading:
+            unknown = set(reading) - set(READINGS)
+            if unknown:
+                raise ValueError(f"unknown readings {sorted(unknown)}")
+            self._lib.ora_set_reading(self._h, *[int(bool(reading.get(k, 0))) for k in READINGS])
 
     def close(self):
         if getattr(self, "_h", None):

@@ -7,9 +7,14 @@
  * test suite, the smoke check and the CPU-baseline leg of the benchmark load
  * it.  It shares no code, header, table or constant with the CUDA library.
  *
- * Build: gcc -O2 -ffp-contract=off -std=c11 -fPIC -shared (no OpenMP, one
- * thread).  Everything is double precision.  Loops follow the paper's
- * equations in the paper's order; nothing is fused or reordered.
+ * Build: gcc -O2 -ffp-contract=off -std=c11 -fPIC -shared, one thread.  The
+ * same file built with -fopenmp spreads the node loops that have no
+ * summation order (collision, streaming, moments, marker interpolation,
+ * adding the spread correction) over host threads; every sum whose order
+ * matters (spreading in ascending marker order, force sums) stays serial, so
+ * both builds give bitwise the same results.  Everything is double
+ * precision.  Loops follow the paper's equations in the paper's order;
+ * nothing is fused or reordered.
  *
  * What one time step computes (section 2, Eqs. 1-8 and 22-29; section 3.3,
  * Eqs. 37-42):
@@ -35,7 +40,9 @@
  *     transform matrix of Eq. 5 (Eq. 4 is garbled in the extracted text).
  *   - (f^eq)* in Eq. 28 interpolates the NODAL equilibria f^eq(rho(x),u(x)).
  *   - The boundary density in f^eq(rho, U) of Eq. 24 is the interpolated
- *     density rho* = sum_i (f_i^eq)*, so the correction conserves mass.
+ *     density rho* = sum_x D rho(x) (= sum_i (f_i^eq)*), so the correction
+ *     conserves mass, and the density parts of f^eq(rho*, U) and (f^eq)*
+ *     cancel exactly.
  *   - Markers are corrected simultaneously (Jacobi): every marker of
  *     iteration n reads the same f^n.
  *   - The correction acts on the post-stream populations, before the moments
@@ -47,6 +54,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORA_Q 9
 
@@ -83,6 +93,12 @@ typedef struct {
   int n_corr;
   int mrt;                  /* 0: BGK, 1: MRT (Eqs. 2, 5, 6) */
   int delta_points;         /* 2, 3 or 4: the delta function of Eq. 15a-c */
+  /* Alternative readings of section 2.3 (all 0 = the readings above); used
+   * only to show how the Couette convergence order depends on them. */
+  int rd_interp_moments;    /* (f^eq)* = f^eq(rho*, j* / rho*), interpolated moments */
+  int rd_rho_b_ref;         /* boundary density rho_b = rho0 instead of rho* */
+  int rd_post_collision;    /* correct the post-collision populations */
+  int rd_unit_ds;           /* spread without the arc length ds (Eq. 26 weight 1) */
   double s_rate[ORA_Q];     /* diagonal of S in Eq. 6 */
   double *f;                /* [9][ny][nx], post-stream state */
   double *g;                /* streaming scratch */
@@ -96,6 +112,7 @@ typedef struct {
   ora_body *bodies;
   double *resid;            /* r^0 .. r^N of the last step */
   double F_euler[2];        /* Eulerian-side force sum of the last step */
+  double *rowF;             /* its per-row partial sums [ny][2] */
   long steps;
 } ora_lattice;
 
@@ -215,6 +232,7 @@ ora_lattice *ora_create(int nx, int ny, double tau, double rho0, const int *bc,
   L->ux = (double *)malloc(sizeof(double) * n);
   L->uy = (double *)malloc(sizeof(double) * n);
   L->resid = (double *)calloc((size_t)n_corr + 1, sizeof(double));
+  L->rowF = (double *)calloc(2 * (size_t)ny, sizeof(double));
   /* rest equilibrium at rho0 */
   double feq[ORA_Q];
   ora_feq(rho0, 0.0, 0.0, feq);
@@ -255,7 +273,7 @@ static double delta_of(const ora_lattice *L, double r) {
 void ora_destroy(ora_lattice *L) {
   if (!L) return;
   free(L->f); free(L->g); free(L->df);
-  free(L->rho); free(L->ux); free(L->uy); free(L->resid);
+  free(L->rho); free(L->ux); free(L->uy); free(L->resid); free(L->rowF);
   free(L->X); free(L->Y); free(L->ds); free(L->dX); free(L->dY);
   free(L->mbody); free(L->bodies); free(L->Uset);
   free(L);
@@ -345,12 +363,24 @@ static int axis_node(int c, int n, int periodic) {
   return (c < 0 || c >= n) ? -1 : c;
 }
 
-/* Eq. 22b with Eq. 28: (f_i^eq)*_l = sum_x D(x - X_l) f_i^eq(rho(x), u(x))
- * over the 4 x 4 support, in row-major node order. */
-static void interpolate_feq(const ora_lattice *L, int l, double *fs) {
+/* The velocity part of Eq. 3: f_i^eq(rho, u) = w_i rho (1 + psi_i(u)). */
+static double psi(int i, double ux, double uy) {
+  double eu = ora_ex[i] * ux + ora_ey[i] * uy;
+  return 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy);
+}
+
+/* Eq. 22b with Eq. 28: interpolation of the nodal equilibria
+ * f_i^eq(rho(x), u(x)) = w_i rho(x) + w_i rho(x) psi_i(u(x)) over the 4 x 4
+ * support, in row-major node order.  Returns the interpolated density
+ * rho* = sum_x D rho(x) and fills phi_i = sum_x D w_i rho(x) psi_i(u(x)),
+ * so that (f_i^eq)* = w_i rho* + phi_i.  (Alternative reading
+ * rd_interp_moments: the equilibrium of the interpolated moments,
+ * phi_i = w_i rho* psi_i(j* / rho*) with j* = sum_x D j(x).) */
+static double interpolate_feq(const ora_lattice *L, int l, double *phi) {
   int px = L->bc[0] == ORA_PERIODIC, py = L->bc[2] == ORA_PERIODIC;
   int bx = (int)floor(L->X[l]) - 1, by = (int)floor(L->Y[l]) - 1;
-  for (int i = 0; i < ORA_Q; ++i) fs[i] = 0.0;
+  double rs = 0.0, jsx = 0.0, jsy = 0.0;
+  for (int i = 0; i < ORA_Q; ++i) phi[i] = 0.0;
   for (int b = 0; b < 4; ++b) {
     int y = axis_node(by + b, L->ny, py);
     if (y < 0) continue;
@@ -359,14 +389,23 @@ static void interpolate_feq(const ora_lattice *L, int l, double *fs) {
       int x = axis_node(bx + a, L->nx, px);
       if (x < 0) continue;
       double wx = delta_of(L, L->X[l] - (double)(bx + a));
-      double p[ORA_Q], rho, jx, jy, feq[ORA_Q];
+      double p[ORA_Q], rho, jx, jy;
       node_pops(L, L->f, x, y, p);
       ora_moments(p, &rho, &jx, &jy);
-      ora_feq(rho, jx / rho, jy / rho, feq);
       double W = wx * wy;
-      for (int i = 0; i < ORA_Q; ++i) fs[i] += W * feq[i];
+      rs += W * rho;
+      if (L->rd_interp_moments) {
+        jsx += W * jx;
+        jsy += W * jy;
+      } else {
+        for (int i = 0; i < ORA_Q; ++i)
+          phi[i] += W * (ora_w[i] * rho * psi(i, jx / rho, jy / rho));
+      }
     }
   }
+  if (L->rd_interp_moments)
+    for (int i = 0; i < ORA_Q; ++i) phi[i] = ora_w[i] * rs * psi(i, jsx / rs, jsy / rs);
+  return rs;
 }
 
 /* Residual of marker l: | (rho u)* / rho* - U_l | from interpolated equilibria. */
@@ -381,6 +420,32 @@ static double marker_residual(const double *fs, const double *U) {
   return sqrt(dx * dx + dy * dy);
 }
 
+/* Interpolation at marker l: fills (f_i^eq)*_l and, when dfm is given, the
+ * deviation of Eq. 28 there; returns the marker's residual.
+ *   delta f_i = f_i^eq(rho_b, U_l) - (f_i^eq)*
+ *             = w_i (rho_b - rho*) + w_i rho_b psi_i(U_l) - phi_i.
+ * With rho_b = rho* (the interpolated density of Eq. 24) the density parts
+ * of the two equilibria are the same number and cancel exactly, so a state
+ * at rest with markers at rest gets no correction at all. */
+static double marker_deviation(const ora_lattice *L, int l, double *dfm) {
+  double phi[ORA_Q], fs[ORA_Q], U[2];
+  double rs = interpolate_feq(L, l, phi);
+  for (int i = 0; i < ORA_Q; ++i) fs[i] = ora_w[i] * rs + phi[i];
+  marker_velocity(L, l, U);
+  double rl = marker_residual(fs, U);
+  if (dfm) {
+    double rho_b = L->rd_rho_b_ref ? L->rho0 : rs;   /* Eq. 24 */
+    for (int i = 0; i < ORA_Q; ++i)                  /* Eq. 28 */
+      dfm[i] = ora_w[i] * (rho_b - rs) + ora_w[i] * rho_b * psi(i, U[0], U[1]) - phi[i];
+  }
+  return rl;
+}
+
+/* Arc-length weight of marker l in Eq. 26 (and in the force of Eq. 29). */
+static double marker_ds(const ora_lattice *L, int l) {
+  return L->rd_unit_ds ? 1.0 : L->ds[l];
+}
+
 /* One correction iteration n (Eqs. 22-27 with Eq. 28), all markers at once.
  * Returns r^n, the largest marker residual before the correction. */
 static double ib_iteration(ora_lattice *L, double *dfm) {
@@ -388,19 +453,14 @@ static double ib_iteration(ora_lattice *L, double *dfm) {
   size_t n = (size_t)L->nx * L->ny;
   double r = 0.0;
   /* Interpolation and deviation at every marker, all from the same f^n. */
+#pragma omp parallel for schedule(static) reduction(max : r)
   for (int l = 0; l < L->nm; ++l) {
-    double fs[ORA_Q], U[2], rho_b = 0.0, fb[ORA_Q];
-    interpolate_feq(L, l, fs);
-    marker_velocity(L, l, U);
-    double rl = marker_residual(fs, U);
+    double rl = marker_deviation(L, l, dfm + (size_t)l * ORA_Q);
     if (rl > r) r = rl;
-    for (int i = 0; i < ORA_Q; ++i) rho_b += fs[i];
-    ora_feq(rho_b, U[0], U[1], fb);                 /* Eq. 24 equilibrium part */
-    for (int i = 0; i < ORA_Q; ++i)
-      dfm[(size_t)l * ORA_Q + i] = fb[i] - fs[i];  /* Eq. 28 */
   }
   /* Eq. 26: spread every deviation, markers in ascending order. */
-  memset(L->df, 0, sizeof(double) * ORA_Q * n);
+#pragma omp parallel for schedule(static)
+  for (size_t k = 0; k < ORA_Q * n; ++k) L->df[k] = 0.0;
   for (int l = 0; l < L->nm; ++l) {
     int bx = (int)floor(L->X[l]) - 1, by = (int)floor(L->Y[l]) - 1;
     for (int b = 0; b < 4; ++b) {
@@ -411,13 +471,14 @@ static double ib_iteration(ora_lattice *L, double *dfm) {
         int x = axis_node(bx + a, L->nx, px);
         if (x < 0) continue;
         double wx = delta_of(L, L->X[l] - (double)(bx + a));
-        double W = wx * wy * L->ds[l];
+        double W = wx * wy * marker_ds(L, l);
         for (int i = 0; i < ORA_Q; ++i)
           L->df[idx(L, i, x, y)] += W * dfm[(size_t)l * ORA_Q + i];
       }
     }
   }
   /* Eq. 27: correct the distribution functions once. */
+#pragma omp parallel for schedule(static)
   for (size_t k = 0; k < ORA_Q * n; ++k) L->f[k] += L->df[k];
   /* Eq. 29, read along its sums: force on each body from the marker
    * deviations (sum over directions of e_i delta f, weighted by the arc
@@ -430,17 +491,27 @@ static double ib_iteration(ora_lattice *L, double *dfm) {
       sx += ora_ex[i] * dfm[(size_t)l * ORA_Q + i];
       sy += ora_ey[i] * dfm[(size_t)l * ORA_Q + i];
     }
-    double Fx = -L->ds[l] * sx, Fy = -L->ds[l] * sy;
+    double Fx = -marker_ds(L, l) * sx, Fy = -marker_ds(L, l) * sy;
     B->F_ib[0] += Fx;
     B->F_ib[1] += Fy;
     /* Eq. 38: torque of the same force about the mass centre */
     B->T_ib += (L->X[l] - B->xc[0]) * Fy - (L->Y[l] - B->xc[1]) * Fx;
   }
-  for (size_t k = 0; k < n; ++k)
-    for (int i = 0; i < ORA_Q; ++i) {
-      L->F_euler[0] -= ora_ex[i] * L->df[(size_t)i * n + k];
-      L->F_euler[1] -= ora_ey[i] * L->df[(size_t)i * n + k];
-    }
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < L->ny; ++y) {
+    double sx = 0.0, sy = 0.0;
+    for (int x = 0; x < L->nx; ++x)
+      for (int i = 0; i < ORA_Q; ++i) {
+        sx -= ora_ex[i] * L->df[idx(L, i, x, y)];
+        sy -= ora_ey[i] * L->df[idx(L, i, x, y)];
+      }
+    L->rowF[2 * y] = sx;
+    L->rowF[2 * y + 1] = sy;
+  }
+  for (int y = 0; y < L->ny; ++y) {   /* rows added in order */
+    L->F_euler[0] += L->rowF[2 * y];
+    L->F_euler[1] += L->rowF[2 * y + 1];
+  }
   return r;
 }
 
@@ -459,11 +530,9 @@ void ora_ib_correct(ora_lattice *L) {
   for (int it = 0; it < L->n_corr; ++it) L->resid[it] = ib_iteration(L, dfm);
   /* final residual from one more interpolation, no correction */
   double r = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : r)
   for (int l = 0; l < L->nm; ++l) {
-    double fs[ORA_Q], U[2];
-    interpolate_feq(L, l, fs);
-    marker_velocity(L, l, U);
-    double rl = marker_residual(fs, U);
+    double rl = marker_deviation(L, l, NULL);
     if (rl > r) r = rl;
   }
   L->resid[L->n_corr] = r;
@@ -603,6 +672,7 @@ static int find_dir(int ex, int ey) {
  * nodes are held at the inlet equilibrium. */
 void ora_record_moments(ora_lattice *L) {
   size_t n = (size_t)L->nx * L->ny;
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < L->ny; ++y)
     for (int x = 0; x < L->nx; ++x) {
       size_t k = (size_t)y * L->nx + x;
@@ -636,49 +706,62 @@ void ora_record_moments(ora_lattice *L) {
  *   extrapolation sides: nothing here (ora_open_boundaries rebuilds the
  *     boundary column before the collision).
  * Populations leaving through an open side are dropped. */
-void ora_collide_stream(ora_lattice *L) {
+/* Post-collision populations of node (x, y): BGK (Eq. 1) or MRT (Eq. 2)
+ * toward the equilibrium of Eq. 3; an equilibrium-inlet node is held at
+ * f^eq(rho0, U_in). */
+static void collide_node(const ora_lattice *L, const double *feq_in, int x, int y,
+                         double *ps) {
+  if (x == 0 && L->bc[0] == ORA_INLET_EQ) {
+    for (int i = 0; i < ORA_Q; ++i) ps[i] = feq_in[i];
+    return;
+  }
+  double p[ORA_Q], rho, jx, jy, feq[ORA_Q];
+  node_pops(L, L->f, x, y, p);
+  ora_moments(p, &rho, &jx, &jy);
+  ora_feq(rho, jx / rho, jy / rho, feq);
+  if (L->mrt)
+    ora_mrt_collide(L->s_rate, p, feq, ps);
+  else
+    for (int i = 0; i < ORA_Q; ++i) ps[i] = p[i] - (p[i] - feq[i]) / L->tau;
+}
+
+/* Streaming (Eq. 1) of the post-collision populations ps of node (x, y)
+ * into L->g with the boundary rules listed above ora_collide_stream.  Every
+ * target slot has exactly one source, so nodes may stream in any order. */
+static void stream_node(ora_lattice *L, int x, int y, const double *ps) {
   int nx = L->nx, ny = L->ny;
-  size_t n = (size_t)nx * ny;
-  for (size_t k = 0; k < ORA_Q * n; ++k) L->g[k] = NAN;
-  double feq_in[ORA_Q];
-  ora_feq(L->rho0, L->inlet_u[0], L->inlet_u[1], feq_in);
-  for (int y = 0; y < ny; ++y)
-    for (int x = 0; x < nx; ++x) {
-      double p[ORA_Q], ps[ORA_Q];
-      if (x == 0 && L->bc[0] == ORA_INLET_EQ) {
-        for (int i = 0; i < ORA_Q; ++i) ps[i] = feq_in[i];
-      } else {
-        double rho, jx, jy, feq[ORA_Q];
-        node_pops(L, L->f, x, y, p);
-        ora_moments(p, &rho, &jx, &jy);
-        ora_feq(rho, jx / rho, jy / rho, feq);
-        if (L->mrt)
-          ora_mrt_collide(L->s_rate, p, feq, ps);
-        else
-          for (int i = 0; i < ORA_Q; ++i) ps[i] = p[i] - (p[i] - feq[i]) / L->tau;
-      }
-      for (int i = 0; i < ORA_Q; ++i) {
-        int tx = x + ora_ex[i], ty = y + ora_ey[i];
-        int sx = tx < 0 ? 0 : (tx >= nx ? 1 : -1);
-        int sy = ty < 0 ? 2 : (ty >= ny ? 3 : -1);
-        if (sx >= 0 && L->bc[sx] == ORA_PERIODIC) { tx = (tx + nx) % nx; sx = -1; }
-        if (sy >= 0 && L->bc[sy] == ORA_PERIODIC) { ty = (ty + ny) % ny; sy = -1; }
-        if (sx < 0 && sy < 0) {
-          L->g[idx(L, i, tx, ty)] = ps[i];
-        } else if ((sx >= 0 && is_open(L->bc[sx])) || (sy >= 0 && is_open(L->bc[sy]))) {
-          /* leaves through an open side */
-        } else if (sx < 0 && L->bc[sy] == ORA_FREESLIP) {
-          L->g[idx(L, find_dir(ora_ex[i], -ora_ey[i]), tx, y)] = ps[i];
-        } else if (sy < 0 && L->bc[sx] == ORA_FREESLIP) {
-          L->g[idx(L, find_dir(-ora_ex[i], ora_ey[i]), x, ty)] = ps[i];
-        } else {
-          int s = sy >= 0 ? sy : sx;
-          double eu = ora_ex[i] * L->wall_u[s][0] + ora_ey[i] * L->wall_u[s][1];
-          L->g[idx(L, find_dir(-ora_ex[i], -ora_ey[i]), x, y)] =
-              ps[i] - 6.0 * ora_w[i] * L->rho0 * eu;
-        }
-      }
+  for (int i = 0; i < ORA_Q; ++i) {
+    int tx = x + ora_ex[i], ty = y + ora_ey[i];
+    int sx = tx < 0 ? 0 : (tx >= nx ? 1 : -1);
+    int sy = ty < 0 ? 2 : (ty >= ny ? 3 : -1);
+    if (sx >= 0 && L->bc[sx] == ORA_PERIODIC) { tx = (tx + nx) % nx; sx = -1; }
+    if (sy >= 0 && L->bc[sy] == ORA_PERIODIC) { ty = (ty + ny) % ny; sy = -1; }
+    if (sx < 0 && sy < 0) {
+      L->g[idx(L, i, tx, ty)] = ps[i];
+    } else if ((sx >= 0 && is_open(L->bc[sx])) || (sy >= 0 && is_open(L->bc[sy]))) {
+      /* leaves through an open side */
+    } else if (sx < 0 && L->bc[sy] == ORA_FREESLIP) {
+      L->g[idx(L, find_dir(ora_ex[i], -ora_ey[i]), tx, y)] = ps[i];
+    } else if (sy < 0 && L->bc[sx] == ORA_FREESLIP) {
+      L->g[idx(L, find_dir(-ora_ex[i], ora_ey[i]), x, ty)] = ps[i];
+    } else {
+      int s = sy >= 0 ? sy : sx;
+      double eu = ora_ex[i] * L->wall_u[s][0] + ora_ey[i] * L->wall_u[s][1];
+      L->g[idx(L, find_dir(-ora_ex[i], -ora_ey[i]), x, y)] =
+          ps[i] - 6.0 * ora_w[i] * L->rho0 * eu;
     }
+  }
+}
+
+static void stream_begin(ora_lattice *L) {
+  size_t n = (size_t)L->nx * L->ny;
+#pragma omp parallel for schedule(static)
+  for (size_t k = 0; k < ORA_Q * n; ++k) L->g[k] = NAN;
+}
+
+/* Outlet copy and inlet hold after streaming, then g becomes f. */
+static void stream_end(ora_lattice *L, const double *feq_in) {
+  int nx = L->nx, ny = L->ny;
   if (L->bc[1] == ORA_OUTLET_ZEROGRAD && nx >= 2)
     for (int y = 0; y < ny; ++y)
       for (int i = 0; i < ORA_Q; ++i)
@@ -691,16 +774,98 @@ void ora_collide_stream(ora_lattice *L) {
   L->g = t;
 }
 
+/* BGK collision (Eq. 1 with Omega_i = -(f_i - f_i^eq)/tau), or MRT (Eq. 2)
+ * after ora_set_mrt, followed by
+ * streaming with the boundary rules:
+ *   periodic: wrap;
+ *   bounce-back (half-way): a population leaving through the wall returns
+ *     to the same node reversed, minus 6 w_i rho0 (e_i . U_w) for a moving
+ *     wall;
+ *   free-slip: specular reflection of the normal component;
+ *   inlet (-x side): the first column is held at f^eq(rho0, U_in);
+ *   outlet (+x side): the populations entering from outside are copied from
+ *     column nx-2;
+ *   extrapolation sides: nothing here (ora_open_boundaries rebuilds the
+ *     boundary column before the collision).
+ * Populations leaving through an open side are dropped. */
+void ora_collide_stream(ora_lattice *L) {
+  double feq_in[ORA_Q];
+  ora_feq(L->rho0, L->inlet_u[0], L->inlet_u[1], feq_in);
+  stream_begin(L);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < L->ny; ++y)
+    for (int x = 0; x < L->nx; ++x) {
+      double ps[ORA_Q];
+      collide_node(L, feq_in, x, y, ps);
+      stream_node(L, x, y, ps);
+    }
+  stream_end(L, feq_in);
+}
+
+/* Alternative reading rd_post_collision: the correction loop acts on the
+ * post-collision populations, between the collision and the streaming. */
+static void step_post_collision(ora_lattice *L) {
+  double feq_in[ORA_Q];
+  ora_feq(L->rho0, L->inlet_u[0], L->inlet_u[1], feq_in);
+  ora_open_boundaries(L);
+  ora_record_moments(L);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < L->ny; ++y)
+    for (int x = 0; x < L->nx; ++x) {
+      double ps[ORA_Q];
+      collide_node(L, feq_in, x, y, ps);
+      for (int i = 0; i < ORA_Q; ++i) L->f[idx(L, i, x, y)] = ps[i];
+    }
+  ora_ib_correct(L);
+  ora_move_bodies(L);
+  stream_begin(L);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < L->ny; ++y)
+    for (int x = 0; x < L->nx; ++x) {
+      double ps[ORA_Q];
+      node_pops(L, L->f, x, y, ps);
+      stream_node(L, x, y, ps);
+    }
+  stream_end(L, feq_in);
+}
+
 /* One full time step in the order stated at the top of this file. */
 void ora_step(ora_lattice *L, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
-    ora_ib_correct(L);
-    ora_move_bodies(L);
-    ora_open_boundaries(L);
-    ora_record_moments(L);
-    ora_collide_stream(L);
+    if (L->rd_post_collision) {
+      step_post_collision(L);
+    } else {
+      ora_ib_correct(L);
+      ora_move_bodies(L);
+      ora_open_boundaries(L);
+      ora_record_moments(L);
+      ora_collide_stream(L);
+    }
     L->steps++;
   }
+}
+
+/* Selects alternative readings of section 2.3 (each 0 or 1; all 0 is the
+ * default reading): equilibria of interpolated moments, rho_b = rho0,
+ * correction of the post-collision populations, spreading without ds. */
+void ora_set_reading(ora_lattice *L, int interp_moments, int rho_b_ref,
+                     int post_collision, int unit_ds) {
+  L->rd_interp_moments = interp_moments;
+  L->rd_rho_b_ref = rho_b_ref;
+  L->rd_post_collision = post_collision;
+  L->rd_unit_ds = unit_ds;
+}
+
+/* Host threads of the -fopenmp build (0: all cores); returns the count in
+ * use, always 1 in the serial build. */
+int ora_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* ---------------------------------------------------------------- access */

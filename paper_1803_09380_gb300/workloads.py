@@ -121,6 +121,25 @@ def couette_analytic(case: Case, x: np.ndarray, y: np.ndarray):
     return ut * sx, ut * sy
 
 
+def couette_paper(r2: float, ratio: float, tau: float, re: float = 10.0,
+                  mrt: bool = True, n_corr: int = 10) -> Case:
+    """Cylindrical Couette flow as section 3.1.2 sets it up: outer radius r2
+    lattice units (the grid spacing is 1/r2 of the outer radius), radius
+    ratio R = r1/r2, relaxation time tau and Re = U1 (r2 - r1)/nu = 10 held
+    fixed under refinement, so the wall speed U1 = Re nu/(r2 - r1) falls as
+    the grid is refined (nu = (tau - 1/2)/3).  The MRT rates of section 3.
+    The periodic box leaves four nodes between the outer ring and its image."""
+    r1 = ratio * r2
+    nu = (tau - 0.5) / 3.0
+    u1 = re * nu / (r2 - r1)
+    n = int(round(2 * r2)) + 8
+    c = couette(n, r1, r2, wall_speed=u1, tau=tau, n_corr=n_corr, center=(n / 2.0, n / 2.0))
+    c.name = f"couette_paper_R{ratio:g}_tau{tau:g}_r{r2:g}"
+    c.mrt = (1.1, 1.25, 1.8) if mrt else None
+    c.meta.update(re=re, ratio=ratio, nu=nu)
+    return c
+
+
 def paper_cylinder(re: float, diameter: int = 40, u0: float = 0.1, mrt: bool = True,
                    n_corr: int = 10) -> Case:
     """Flow past a fixed cylinder as section 3.2 sets it up: a 40D x 20D
