@@ -22,8 +22,11 @@ reading of section 2.3 switched on at a time (oracle READINGS), and with the
 BGK collision instead of MRT.
 
 Calls only the oracle and the workload geometry.  Run from the repository
-root:  python tests/golden/make_couette_paper.py   (about 30 min on 8 cores)
+root:  python tests/golden/make_couette_paper.py [--cache FILE]
+(about 30 min on 8 cores).  With --cache, every finished run is stored in
+FILE and reused by a later invocation, so an interrupted run resumes.
 """
+import argparse
 import json
 import math
 import os
@@ -99,7 +102,30 @@ def slopes(runs):
     return out
 
 
+class Cache:
+    """Finished runs keyed by their parameters (optional)."""
+
+    def __init__(self, path):
+        self.path = path
+        self.runs = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.runs = json.load(f)
+
+    def get(self, key):
+        return self.runs.get(key)
+
+    def put(self, key, rec):
+        self.runs[key] = rec
+        if self.path:
+            with open(self.path, "w") as f:
+                json.dump(self.runs, f, indent=1)
+
+
 def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--cache", default=None)
+    cache = Cache(ap.parse_args().cache)
     threaded = oracle.threaded_available()
     cores = oracle.set_threads(0) if threaded else 1
     doc = {"source": "FP64 oracle, cylindrical Couette flow in the setup of section 3.1.2 "
@@ -111,9 +137,13 @@ def main():
     for ratio, tau, levels in MAIN:
         runs = []
         for r2 in levels:
-            t = time.time()
-            rec = run(wl.couette_paper(r2, ratio, tau), threaded=threaded)
-            rec["seconds"] = round(time.time() - t, 1)
+            key = f"main R{ratio} tau{tau} r{r2}"
+            rec = cache.get(key)
+            if rec is None:
+                t = time.time()
+                rec = run(wl.couette_paper(r2, ratio, tau), threaded=threaded)
+                rec["seconds"] = round(time.time() - t, 1)
+                cache.put(key, rec)
             print(ratio, tau, json.dumps(rec), flush=True)
             runs.append(rec)
         doc["main"].append({"ratio": ratio, "tau": tau, "runs": runs, "slopes": slopes(runs)})
@@ -121,10 +151,14 @@ def main():
     for name, reading in READING_VARIANTS:
         runs = []
         for r2 in READING_LEVELS:
-            case = wl.couette_paper(r2, 0.5, 0.65, mrt=(name != "bgk"))
-            t = time.time()
-            rec = run(case, reading=reading, threaded=threaded)
-            rec["seconds"] = round(time.time() - t, 1)
+            key = f"reading {name} r{r2}"
+            rec = cache.get(key)
+            if rec is None:
+                case = wl.couette_paper(r2, 0.5, 0.65, mrt=(name != "bgk"))
+                t = time.time()
+                rec = run(case, reading=reading, threaded=threaded)
+                rec["seconds"] = round(time.time() - t, 1)
+                cache.put(key, rec)
             print(name, json.dumps(rec), flush=True)
             runs.append(rec)
         doc["readings"].append({"reading": name, "ratio": 0.5, "tau": 0.65, "runs": runs,

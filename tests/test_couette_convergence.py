@@ -1,13 +1,20 @@
 """Cylindrical Couette flow (section 3.1.2): convergence of the steady state
-to the analytic profile of Eq. 34 under grid refinement.
+to the analytic profile of Eq. 34 under grid refinement, at the workload's
+scaling (radii 0.156 N and 0.39 N, wall speed and tau fixed).
 
 The stored sweep (tests/golden/couette_sweep.json) was written by
-tests/golden/make_couette_sweep.py, which calls only the oracle.  Under the
-sweep's scaling (radii 0.156 N and 0.39 N, wall speed and tau fixed) the
-method converges at first order in the relative L2 norm: the diffuse
-interface places the effective wall off the marker ring by a fraction of
-a lattice spacing.  The pins: the error falls monotonically, with slope
-<= -0.9, and the stored values are reproduced by the current oracle."""
+tests/golden/make_couette_sweep.py, which calls only the oracle.  The order
+these pins accept -- first, slope <= -0.9 in the relative L2 norm -- is the
+order the paper's own setup gives in the non-dimensional velocity: run
+through the oracle with Re 10, tau 0.65 / 0.85 and radius ratio 0.5 / 0.8
+under diffusive scaling (tests/golden/couette_paper.json,
+tests/test_couette_paper.py), the error in u / U1 falls at first order for
+every setup and every alternative reading of section 2.3, while Eq. 35's
+norm in lattice units falls at second order -- the paper's Fig. 5 claim.
+The diffuse interface places the effective wall off the marker ring by a
+fraction of a lattice spacing.  The pins: the error falls monotonically,
+with slope <= -0.9, and the stored values are reproduced by the current
+oracle."""
 import json
 import math
 import os
