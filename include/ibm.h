@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define IBM_ABI_VERSION 3
+#define IBM_ABI_VERSION 4
 
 typedef struct ibm_ctx *ibm_handle; /* opaque, library-owned */
 
@@ -177,18 +177,36 @@ ibm_status ibm_add_markers(ibm_handle h, const double *xy, const double *ds,
 /* Advances nsteps time steps.  One step: the N-iteration correction loop on
  * the post-stream state (Eqs. 22-28; residuals r^0..r^N recorded), body
  * force and torque (Eq. 29), the body update (Eqs. 37-42) and marker motion,
- * then the fused BGK collide + AA-pattern stream over every node. */
+ * then the fused BGK collide + AA-pattern stream over every node.  Returns
+ * once the steps are enqueued, except with corr_tol > 0: then it waits for
+ * them and returns IBM_WARN_NOT_CONVERGED if any step since the last
+ * synchronising call ended with r^N > corr_tol (or the error of a failed
+ * step).  IBM_ERR_INVALID after a failed ibm_add_markers (destroy the
+ * lattice). */
 ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags);
 
 /* Copies a field into host_dst (n_elems doubles, which must equal the
- * field's size) after synchronising the handle's stream. */
+ * field's size) after synchronising the handle's stream.  The fields are the
+ * moments of Eq. 7 of the last corrected pre-collision state (RHO, UX, UY),
+ * the post-stream populations of Eq. 1 (F), the body state of Eqs. 41-42
+ * with the force and torque of Eq. 29 and Eq. 38 of the last step (BODIES),
+ * the no-slip residuals r^0..r^N of the correction loop of section 2.3
+ * (RESIDUAL; returns IBM_WARN_NOT_CONVERGED when corr_tol > 0 and r^N is
+ * above it) and the marker positions X_l (MARKERS).  Errors: IBM_ERR_INVALID
+ * for an unknown field or a wrong n_elems, and the device errors of
+ * ibm_sync. */
 ibm_status ibm_read_fields(ibm_handle h, int field, double *host_dst, size_t n_elems);
 
 /* Writes IBM_FIELD_F (raw post-stream populations) or IBM_FIELD_MACRO_INIT
  * (equilibrium of the given rho, u) from host_src, n_elems doubles. */
 ibm_status ibm_write_fields(ibm_handle h, int field, const double *host_src, size_t n_elems);
 
-/* Blocks until the handle's queued work is done; reports device errors. */
+/* Blocks until the handle's queued work is done; reports device errors:
+ * IBM_ERR_BOUNDS (a capacity check tripped: markers too dense),
+ * IBM_ERR_TIMEOUT (a bounded grid-barrier wait ran out), IBM_ERR_DIVERGED
+ * (a non-finite residual, or a NaN/Inf found by the watchdog), and the
+ * warning IBM_WARN_NOT_CONVERGED (corr_tol > 0 and some step since the last
+ * report ended with r^N above it; reported once). */
 ibm_status ibm_sync(ibm_handle h);
 
 /* Device time of the collide+stream launches bracketed since the last call
@@ -226,7 +244,21 @@ enum {
                            markers, 3 per 4 SMs above that; n > 0 = min(n, SMs).  2..16 CTAs
                            run as one thread-block cluster when the device can schedule it.
                            Results do not depend on it. */
-  IBM_OPT_IB_THREADS = 2 /* threads per correction-kernel CTA: 256 (default), 512 or 1024 */
+  IBM_OPT_IB_THREADS = 2, /* threads per correction-kernel CTA: 256 (default), 512 or 1024 */
+  IBM_OPT_WATCHDOG_STEPS = 3, /* K > 0: after every K steps (at the next 8-step block boundary)
+                           scan every stored population for NaN/Inf; a hit makes the next
+                           synchronising call return IBM_ERR_DIVERGED.  0 (default): no scan.
+                           Independently of it, a non-finite no-slip residual r^N is
+                           detected by the correction kernel every step. */
+  IBM_OPT_BARRIER_LIMIT_US = 4, /* wait limit of the correction kernel's global-memory grid
+                           barrier in microseconds, [100, 6e7] (default 2 s); a wait that runs
+                           out makes the next synchronising call return IBM_ERR_TIMEOUT */
+  IBM_OPT_TEST_DROP_ARRIVAL = 5 /* testing the timeout path only: 1 makes the last CTA of the
+                           correction kernel skip its arrival at the first grid barrier of each
+                           step, so the other CTAs' waits run out (bounded by
+                           IBM_OPT_BARRIER_LIMIT_US).  Only grids that wait at the
+                           global-memory barrier (more than 16 CTAs) are affected.  The
+                           lattice's results are then wrong; destroy it afterwards. */
 };
 
 /* Chooses the correction kernel's CTA count by measurement: for each of the
@@ -250,7 +282,11 @@ ibm_status ibm_autotune_ib(ibm_handle h, const int *candidates, int n, int steps
  * thread-block cluster, which the hardware schedules as a whole. */
 ibm_status ibm_set_option(ibm_handle h, int option, long long value);
 
-/* Frees every device and host resource of h (NULL is a no-op). */
+/* Frees every device and host resource of h (NULL is a no-op): the
+ * populations of Eq. 1, the marker and band arrays of the correction loop
+ * (section 2.3) and the body records of Eqs. 37-42.  Synchronises the
+ * handle's stream first; returns IBM_ERR_CUDA when that reports an error
+ * (the resources are freed all the same). */
 ibm_status ibm_destroy(ibm_handle h);
 
 /* Message for the last failure on h (thread-local for h == NULL). */
@@ -289,6 +325,17 @@ typedef struct {
   int ib_markers_per_cta;     /* a case with M markers runs its correction loop on
                                  ceil(M / this) CTAs, at most 16 (one thread-block
                                  cluster; one CTA when M <= this); <= 0: 512 */
+  int batched;                /* 0: each resident case is stepped by its own graph
+                                 launches on its own stream; 1: one persistent kernel per
+                                 round of steps_per_launch steps advances every resident
+                                 case (FP32 and 16-bit storage; FP64 cases are refused):
+                                 its CTAs take each step's correction tasks and
+                                 collide+stream tiles of all cases from one work queue */
+  int tile_nodes;             /* batched: lattice nodes per collide+stream tile (whole
+                                 rows, at least one); <= 0: 32768 */
+  int corr_first;             /* batched: order of a step's tasks in the queue.  1 or <= 0
+                                 (default): the correction tasks of every case, then all
+                                 tiles; 2: case by case, its correction tasks then its tiles */
 } ibm_server_desc;
 
 enum { IBM_OUT_MACRO = 1, IBM_OUT_BODIES = 2, IBM_OUT_RESIDUAL = 4 };
@@ -332,6 +379,19 @@ ibm_status ibm_server_wait(ibm_server s, long long case_id);
 ibm_status ibm_server_result(ibm_server s, long long case_id, int field, double *host_dst, size_t n_elems);
 ibm_status ibm_server_release(ibm_server s, long long case_id);   /* drops stored results */
 ibm_status ibm_server_get_stats(ibm_server s, ibm_server_stats *out);
+/* Batched mode's autotuner (no counterpart in the paper): on an idle server,
+ * runs the n sample cases for every combination of the candidate tile sizes
+ * (nodes per collide+stream tile), markers per correction CTA and task
+ * orders (1 and 2, see corr_first), times each run (all samples submitted
+ * at once, wall clock to the last result), keeps the fastest setting and
+ * returns it.  The sample runs do not enter the server's statistics.  NULL
+ * or empty candidate lists take defaults (tiles 8192, 16384, 32768, 65536;
+ * markers per CTA 256, 512, 1024).  Errors: IBM_ERR_INVALID when the server
+ * is not batched or not idle, or a sample is invalid; a failed sample run's
+ * status otherwise. */
+ibm_status ibm_server_autotune(ibm_server s, const ibm_case_desc *samples, int n, const int *tile_nodes,
+                               int n_tiles, const int *markers_per_cta, int n_mpc, int *best_tile_nodes,
+                               int *best_markers_per_cta, int *best_corr_first, double *best_seconds);
 ibm_status ibm_server_destroy(ibm_server s);
 const char *ibm_server_last_error(ibm_server s);
 
@@ -345,16 +405,19 @@ const char *ibm_server_last_error(ibm_server s);
  *
  * The caller passes every input and output as device memory it owns:
  *   f          [9][ny][nx] post-stream populations (double for IBM_FP64,
- *              float for IBM_FP32), corrected in place (N iterations of
- *              Eqs. 22-28 and the summed correction of Eq. 27; no collision,
- *              no streaming); the lattice is periodic in x and y;
+ *              float for IBM_FP32), corrected in place by the N-iteration
+ *              correction loop of ibm_step (no collision, no streaming); the
+ *              lattice is periodic in x and y;
  *   xy, ds     2n interleaved marker positions and n arc lengths (double);
  *   uvel       2n interleaved marker velocities (double);
- *   resid_out  n_corr + 1 doubles, r^0 .. r^N (may be NULL);
- *   force_out  2 doubles, the force of Eq. 29 summed over all markers (may
- *              be NULL).
+ *   resid_out  n_corr + 1 doubles, the residuals r^0 .. r^N (may be NULL);
+ *   force_out  2 doubles, the force on all markers together (may be NULL).
  * The work runs on cuda_stream (NULL: the legacy default stream) on the
- * current device, and the call returns after synchronising that stream.
+ * current device as one CTA per kernel, and the call returns after
+ * synchronising that stream.  On entry it clears the calling thread's
+ * pending CUDA launch error (left by earlier work), so that it reports only
+ * errors of its own work.  When the call fails, the contents of f, resid_out
+ * and force_out are undefined.
  *
  * Nothing is allocated: every intermediate array lives in one fixed 8 MiB
  * device array that the library reserves when it is loaded and that every
@@ -362,10 +425,11 @@ const char *ibm_server_last_error(ibm_server s);
  * nx * ny <= 262144, 1 <= n <= 512 markers, 0 <= n_corr <= 64; larger
  * requests return IBM_ERR_INVALID with a message in ibm_last_error(NULL).
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
- * share the array and it keeps the last call's contents (the call clears
- * what must start empty); calls that overlap on the GPU -- from several host
- * threads or streams at once -- race and give wrong results. */
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins.  All calls share the array and it keeps the last call's contents
+ * (the call clears what must start empty); calls that overlap on the GPU --
+ * from several host threads or streams at once -- race and give wrong
+ * results. */
 ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void *f, int n_markers, const double *xy,
                                   const double *ds, const double *uvel, int n_corr, double *resid_out,
                                   double *force_out, void *cuda_stream);

@@ -16,8 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibm.so")
-SOURCES = ["ibm_api.cu", "ibm_lbm.cu", "ibm_ib.cu", "ibm_noalloc.cu", "ibm_serve.cu"]
-HEADERS = ["ibm_device.cuh", "ibm_internal.h", "ibm_k1.cuh"]
+SOURCES = ["ibm_api.cu", "ibm_lbm.cu", "ibm_ib.cu", "ibm_noalloc.cu", "ibm_serve.cu",
+           "ibm_batch_f32.cu", "ibm_batch_f16.cu", "ibm_batch_bf16.cu"]
+HEADERS = ["ibm_device.cuh", "ibm_internal.h", "ibm_k1.cuh", "ibm_ib.cuh", "ibm_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr"]

@@ -122,6 +122,15 @@ ibm_status check_device_flags(Ctx* h) {
     return fail(h, IBM_ERR_BOUNDS, "a marker couples to more than 64 markers (markers too dense)");
   if (ctr[CTR_ERR] & ERR_BARRIER)
     return fail(h, IBM_ERR_TIMEOUT, "the correction-loop grid barrier timed out");
+  if (ctr[CTR_ERR] & ERR_DIVERGED)
+    return fail(h, IBM_ERR_DIVERGED, "non-finite population or residual (the state has diverged)");
+  if (ctr[CTR_ERR] & WARN_NOT_CONV) {
+    // a warning: reported once, then cleared on the device
+    const int rest = ctr[CTR_ERR] & ~WARN_NOT_CONV;
+    IBM_CK(h, cudaMemcpyAsync(h->dctr + CTR_ERR, &rest, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    IBM_CK(h, cudaStreamSynchronize(h->stream));
+    return fail(h, IBM_WARN_NOT_CONVERGED, "no-slip residual above corr_tol after n_corr iterations");
+  }
   return IBM_OK;
 }
 
@@ -178,6 +187,16 @@ ibm_status fold_events(Ctx* h) {
   h->acc_n += h->ev_used;
   h->ev_used = 0;
   return IBM_OK;
+}
+
+// The NaN/Inf scan of the whole lattice after every watchdog_steps steps
+// (checked between graph replays, so with blocks of steps it runs at the
+// first block boundary at or after the due step).
+void watchdog_if_due(Ctx& c) {
+  if (c.watchdog_steps <= 0 || c.watch_due < c.watchdog_steps) return;
+  launch_watchdog(c, c.stream);
+  c.launches += 1;
+  c.watch_due = 0;
 }
 
 // CTAs of the correction kernel: one for small boundaries, 3/4 of the SMs
@@ -284,6 +303,8 @@ ibm_status upload_markers(Ctx* h) {
                                            (size_t)c.bcap * kBandCap, c.stream));
   IBM_CK(h, cudaMemsetAsync(c.dbcnt, 0, sizeof(int) * c.bcap, c.stream));
   IBM_CK(h, cudaStreamSynchronize(c.stream));   // host vectors are temporaries
+  c.dev_nm = c.nm;
+  c.dev_nb = c.nb;
   c.band_valid = false;
   destroy_graphs(c);
   return IBM_OK;
@@ -292,16 +313,19 @@ ibm_status upload_markers(Ctx* h) {
 // Device -> host copy of the moving state before markers are re-uploaded.
 ibm_status download_moving_state(Ctx* h) {
   Ctx& c = *h;
-  if (c.nm == 0 || !c.any_moving) return IBM_OK;
-  std::vector<char> ux(c.r_bytes * c.nm), uy(c.r_bytes * c.nm);
-  IBM_CK(h, cudaMemcpyAsync(c.hX.data(), c.dX, 8 * c.nm, cudaMemcpyDeviceToHost, c.stream));
-  IBM_CK(h, cudaMemcpyAsync(c.hY.data(), c.dY, 8 * c.nm, cudaMemcpyDeviceToHost, c.stream));
-  IBM_CK(h, cudaMemcpyAsync(ux.data(), c.dUx, c.r_bytes * c.nm, cudaMemcpyDeviceToHost, c.stream));
-  IBM_CK(h, cudaMemcpyAsync(uy.data(), c.dUy, c.r_bytes * c.nm, cudaMemcpyDeviceToHost, c.stream));
-  IBM_CK(h, cudaMemcpyAsync(c.hbodies.data(), c.dbodies, sizeof(BodyDev) * c.nb, cudaMemcpyDeviceToHost,
+  // the markers and bodies the device holds (appended ones not yet uploaded
+  // have only their host copy)
+  const int M = c.dev_nm, B = c.dev_nb;
+  if (M == 0 || !c.any_moving) return IBM_OK;
+  std::vector<char> ux(c.r_bytes * M), uy(c.r_bytes * M);
+  IBM_CK(h, cudaMemcpyAsync(c.hX.data(), c.dX, 8 * M, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.hY.data(), c.dY, 8 * M, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(ux.data(), c.dUx, c.r_bytes * M, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(uy.data(), c.dUy, c.r_bytes * M, cudaMemcpyDeviceToHost, c.stream));
+  IBM_CK(h, cudaMemcpyAsync(c.hbodies.data(), c.dbodies, sizeof(BodyDev) * B, cudaMemcpyDeviceToHost,
                             c.stream));
   IBM_CK(h, cudaStreamSynchronize(c.stream));
-  for (int l = 0; l < c.nm; ++l) {
+  for (int l = 0; l < M; ++l) {
     c.hUx[l] = c.r_bytes == 8 ? ((double*)ux.data())[l] : ((float*)ux.data())[l];
     c.hUy[l] = c.r_bytes == 8 ? ((double*)uy.data())[l] : ((float*)uy.data())[l];
   }
@@ -475,14 +499,10 @@ ibm_status ibm::create_lattice(const ibm_lattice_desc* desc, ibm_handle* out, cu
   return IBM_OK;
 }
 
-extern "C" {
-
-ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
-  return ibm::create_lattice(desc, out, nullptr);
-}
-
-ibm_status ibm_add_markers(ibm_handle h, const double* xy, const double* ds, int n,
-                           const ibm_body_desc* body, int* body_id_out) {
+// One body and its markers appended to the host copy; with `upload` the
+// marker arrays are then re-uploaded (as ibm_add_markers does).
+static ibm_status add_body(ibm_handle h, const double* xy, const double* ds, int n, const ibm_body_desc* body,
+                           int* body_id_out, bool upload) {
   if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
   if (!xy || n <= 0 || !body) return fail(h, IBM_ERR_INVALID, "xy, n > 0 and body are required");
   try {
@@ -562,8 +582,13 @@ ibm_status ibm_add_markers(ibm_handle h, const double* xy, const double* ds, int
     c.nm += n;
     const int id = c.nb++;
     if (b.kind != IBM_BODY_FIXED) c.any_moving = true;
-    ibm_status st = upload_markers(h);
-    if (st != IBM_OK) return st;
+    if (upload) {
+      ibm_status st = upload_markers(h);
+      if (st != IBM_OK) {
+        c.broken = true;                 // marker arrays are partly released
+        return st;
+      }
+    }
     if (body_id_out) *body_id_out = id;
     return IBM_OK;
   } catch (const std::bad_alloc&) {
@@ -571,6 +596,43 @@ ibm_status ibm_add_markers(ibm_handle h, const double* xy, const double* ds, int
   } catch (...) {
     return fail(h, IBM_ERR_INVALID, "unexpected error in ibm_add_markers");
   }
+}
+
+// Every body of a case, then one upload of the marker arrays (the serving
+// layer's admission: one round trip instead of one per body).
+ibm_status ibm::add_bodies(ibm_handle h, int nbodies, const ibm_body_desc* bodies, const int* nmark,
+                           const double* xy, const double* ds) {
+  if (!h) return fail(nullptr, IBM_ERR_INVALID, "handle is NULL");
+  size_t off = 0;
+  for (int b = 0; b < nbodies; ++b) {
+    ibm_status st = add_body(h, xy + 2 * off, ds ? ds + off : nullptr, nmark[b], &bodies[b], nullptr, false);
+    if (st != IBM_OK) {
+      h->broken = true;                  // the host copy holds bodies the device has not seen
+      return st;
+    }
+    off += nmark[b];
+  }
+  if (nbodies == 0) return IBM_OK;
+  try {
+    DeviceGuard guard(h->device);
+    ibm_status st = upload_markers(h);
+    if (st != IBM_OK) h->broken = true;
+    return st;
+  } catch (const std::bad_alloc&) {
+    h->broken = true;
+    return fail(h, IBM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+extern "C" {
+
+ibm_status ibm_create_lattice(const ibm_lattice_desc* desc, ibm_handle* out) {
+  return ibm::create_lattice(desc, out, nullptr);
+}
+
+ibm_status ibm_add_markers(ibm_handle h, const double* xy, const double* ds, int n,
+                           const ibm_body_desc* body, int* body_id_out) {
+  return add_body(h, xy, ds, n, body, body_id_out, true);
 }
 
 ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
@@ -581,6 +643,8 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
     DeviceGuard guard(h->device);
     if (!guard.ok) return fail(h, IBM_ERR_CUDA, "cannot select the CUDA device");
     Ctx& c = *h;
+    if (c.broken)
+      return fail(h, IBM_ERR_INVALID, "a failed marker upload left this lattice unusable; destroy it");
     const bool timing = (flags & IBM_STEP_TIME_KERNELS) != 0;
     const bool use_graph = !(flags & (IBM_STEP_NO_GRAPH | IBM_STEP_TIME_KERNELS));
     if (timing && c.ev.empty()) {
@@ -607,6 +671,8 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
         IBM_CK(h, cudaGraphLaunch(c.graph_block[parity], c.stream));
         c.launches += (long long)kBlockSteps * kernels_per_step(c);
         c.steps += kBlockSteps;
+        c.watch_due += kBlockSteps;
+        watchdog_if_due(c);
         k += kBlockSteps;
         continue;
       }
@@ -632,8 +698,13 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
       c.parity ^= 1;
       c.launches += kernels_per_step(c);
       c.steps += 1;
+      c.watch_due += 1;
+      watchdog_if_due(c);
     }
     IBM_CK(h, cudaGetLastError());
+    // with a tolerance, the call waits for its steps and reports a residual
+    // above it (or any device error) at once
+    if (c.desc.corr_tol > 0 && c.nm > 0) return sync_stream(h);
     return IBM_OK;
   } catch (...) {
     return fail(h, IBM_ERR_INVALID, "unexpected error in ibm_step");
@@ -912,6 +983,24 @@ ibm_status ibm_set_option(ibm_handle h, int option, long long value) {
     h->ib_cluster_max = -1;
     choose_ib_grid(*h);
     destroy_graphs(*h);
+    return IBM_OK;
+  }
+  if (option == IBM_OPT_WATCHDOG_STEPS) {
+    if (value < 0 || value > (1LL << 40)) return fail(h, IBM_ERR_INVALID, "IBM_OPT_WATCHDOG_STEPS out of range");
+    h->watchdog_steps = (int)std::min<long long>(value, 1 << 30);
+    h->watch_due = 0;
+    return IBM_OK;
+  }
+  if (option == IBM_OPT_BARRIER_LIMIT_US || option == IBM_OPT_TEST_DROP_ARRIVAL) {
+    if (option == IBM_OPT_BARRIER_LIMIT_US && (value < 100 || value > 60000000))
+      return fail(h, IBM_ERR_INVALID, "IBM_OPT_BARRIER_LIMIT_US must be in [100, 6e7]");
+    if (option == IBM_OPT_TEST_DROP_ARRIVAL && value != 0 && value != 1)
+      return fail(h, IBM_ERR_INVALID, "IBM_OPT_TEST_DROP_ARRIVAL must be 0 or 1");
+    DeviceGuard guard(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (option == IBM_OPT_BARRIER_LIMIT_US) h->bar_limit_ns = value * 1000LL;
+    else h->test_drop_arrival = (int)value;
+    destroy_graphs(*h);                  // the kernels take both as arguments
     return IBM_OK;
   }
   if (option != IBM_OPT_IB_CTAS) return fail(h, IBM_ERR_INVALID, "unknown option");

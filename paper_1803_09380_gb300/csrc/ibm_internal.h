@@ -22,7 +22,9 @@ struct BodyDev {
   double F_ib[2], T_ib;     // Eq. 29 sums of the last step (no internal-mass terms)
 };
 
-enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4, ERR_BARRIER = 8, ERR_G_CAP = 16 };
+enum { ERR_BAND_CAP = 1, ERR_LIST_CAP = 2, ERR_SEG_CAP = 4, ERR_BARRIER = 8, ERR_G_CAP = 16,
+       ERR_DIVERGED = 32,      // a non-finite residual or population (the watchdog)
+       WARN_NOT_CONV = 64 };   // r^N above corr_tol (a warning, cleared once reported)
 
 // One entry of a band node's list of covering markers: marker id and its
 // spreading weight W_l(x) ds_l.
@@ -37,7 +39,7 @@ constexpr int kGCap = 64;                        // coupled markers per marker (
 constexpr int kBlockSteps = 8;       // steps per multi-step graph (even: parity returns)
 constexpr int kForceChunk = 128;                 // markers per partial force sum
 constexpr int kSmallIbMarkers = 512;             // up to this many markers: one correction CTA
-constexpr long long kBarrierCycles = 4000000000LL; // ~2 s at 2 GHz: grid-barrier wait limit
+constexpr long long kBarrierNs = 2000000000LL;   // grid-barrier wait limit: 2 s
 
 // Device counters: band nodes, band row segments, error bits.
 enum { CTR_NBAND = 0, CTR_NSEG = 1, CTR_ERR = 2, CTR_COUNT = 4 };
@@ -79,6 +81,7 @@ struct Ctx {
   std::vector<int> hmbody;
   std::vector<BodyDev> hbodies;
   int nm = 0, nb = 0;
+  int dev_nm = 0, dev_nb = 0;   // markers and bodies of the last upload
   bool any_moving = false;
 
   // marker / band device arrays (sized for nm markers, 16 nm band nodes)
@@ -118,6 +121,11 @@ struct Ctx {
   int ib_grid_opt = 0;                       // caller's choice (IBM_OPT_IB_CTAS), 0 = by size
   bool band_collide = true;                  // stream the band segments after the correction
   bool band_valid = false;
+  bool broken = false;                       // a failed marker upload left arrays unset
+  long long bar_limit_ns = kBarrierNs;       // grid-barrier wait limit (IBM_OPT_BARRIER_LIMIT_US)
+  int test_drop_arrival = 0;                 // IBM_OPT_TEST_DROP_ARRIVAL
+  int watchdog_steps = 0;                    // IBM_OPT_WATCHDOG_STEPS (0: off)
+  long long watch_due = 0;                   // steps since the last watchdog scan
 
   // CUDA graphs of one step, per parity and macro flag
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -232,10 +240,45 @@ void set_thread_error(const char* msg);
 // every device allocation of the handle is stream-ordered on its stream
 // (no device-wide synchronisation when the handle is destroyed).
 ibm_status create_lattice(const ibm_lattice_desc* desc, ibm_handle* out, cudaMemPool_t pool);
+// ibm_add_markers for every body of a case (nmark[b] markers each, xy and ds
+// concatenated body after body, ds may be NULL) with one upload at the end.
+ibm_status add_bodies(ibm_handle h, int nbodies, const ibm_body_desc* bodies, const int* nmark, const double* xy,
+                      const double* ds);
 
 // ibm_lbm.cu
 void launch_collide_stream(const Ctx& h, int parity, bool macro, int mode, cudaStream_t s);
 void launch_fields(const Ctx& h, int op, const double* dev_in, double* dev_out, cudaStream_t s);
+// Scan of every stored population for NaN/Inf; sets ERR_DIVERGED.
+void launch_watchdog(const Ctx& h, cudaStream_t s);
+
+// ibm_batch.cu: the batched serving kernel (one persistent kernel over a
+// task queue advancing many lattices).  The table a launch reads is
+// [BatchHead, padded to kBatchHeadBytes][cap case records][tasks of one
+// round as (case slot, task) int2].
+constexpr int kBatchThreads = 256;
+constexpr int kBatchHeadBytes = 256;
+struct BatchHead {
+  unsigned int next;         // next task index to hand out
+  unsigned int err;          // nonzero: a wait ran out (the launch's results are void)
+  int per_round;             // tasks of one round (one time step of every case)
+  int rounds;                // rounds of this launch
+  long long wait_ns;         // limit of every wait
+  unsigned long long t_start;  // %globaltimer when the first task was taken
+};
+// One storage precision's batched kernel (instantiated for FP32, FP16 and
+// BF16 storage in ibm_batch_f32.cu, ibm_batch_f16.cu, ibm_batch_bf16.cu).
+template <int P>
+struct BatchOps {
+  static size_t case_bytes();
+  // CTAs of the batched kernel the device holds at once (0: cannot run).
+  static int grid();
+  // The case record of lattice h for one launch, written to host memory dst.
+  static void record(const Ctx& h, void* dst, int steps, int macro_last, int corr, int tiles, int rows,
+                     long long wait_ns);
+  static void launch(void* dev_table, int cap, int grid, cudaStream_t s);
+  // %globaltimer at which the case of record rec finished its last task
+  static unsigned long long end_time(const void* rec);
+};
 
 // ibm_ib.cu
 void launch_band_build(const Ctx& h, cudaStream_t s);

@@ -425,4 +425,111 @@ __device__ __forceinline__ void odd_vec(const Geom& g, const StepConsts<typename
   }
 }
 
+// ------------------------------------------------------------------ spans
+// One warp's share of a collide+stream step: the span of 32 * VEC
+// consecutive nodes of row y that starts at node wrow * 32 * VEC (all 32
+// lanes of the warp call it together).  PAR 0: even step, 1: odd step.
+// MODE K1_ALL: every node.  MODE K1_MAIN: every node outside the 32-node
+// segments that hold band nodes (segflag).  Even step: per lane, aligned
+// vectors (ragged row ends node by node).  Odd step: spans without boundary
+// or ragged nodes take the vector path (lanes whose nodes lie in band
+// segments sit out); the others go node by node through the boundary-aware
+// path.  Extrapolation columns are left to open_column.
+template <int P, int PAR, bool MACRO, int MODE, bool MRT>
+__device__ __forceinline__ void k1_span(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                        typename Prec<P>::S* __restrict__ A,
+                                        typename Prec<P>::R* __restrict__ mac,
+                                        const int* __restrict__ segflag, int nseg_x, int y, int wrow,
+                                        int lane) {
+  constexpr int VEC = PAR ? VecTraits<P>::VEC_ODD : VecTraits<P>::VEC;
+  const int xw = wrow * (32 * VEC);
+  if (xw >= g.nx) return;                               // whole warp
+  const int x0 = xw + lane * VEC;
+  const bool flagged = MODE == K1_MAIN && x0 < g.nx && segflag[y * nseg_x + x0 / kSegW] != 0;
+  if (PAR == 0) {
+    if (flagged || x0 >= g.nx) return;
+    const bool nee = has_nee(g) && (nee_column(g, x0) || nee_column(g, min(x0 + VEC, g.nx) - 1));
+    if (x0 + VEC <= g.nx && !nee) {
+      even_vec<P, MACRO, MRT>(g, c, A, mac, x0, y);
+    } else {
+      for (int x = x0; x < g.nx && x < x0 + VEC; ++x)
+        if (!nee_column(g, x)) even_node<P, MACRO, MRT>(g, c, A, mac, x, y);
+    }
+    return;
+  }
+  const bool closed_x = g.bc[0] != BC_PERIODIC;
+  const int x_special =
+      closed_x ? ((g.bc[1] == BC_OUTLET || g.bc[1] == BC_OUTLET_NEE) ? g.nx - 2 : g.nx - 1) : g.nx;
+  const bool edge = (g.bc[2] != BC_PERIODIC && (y == 0 || y == g.ny - 1)) ||
+                    (closed_x && xw == 0) || (xw + 32 * VEC > x_special) || (xw + 32 * VEC > g.nx);
+  if (edge) {
+    for (int k = 0; k < VEC; ++k) {
+      const int x = x0 + k;
+      if (x >= g.nx) break;
+      if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) continue;
+      if (nee_column(g, x)) continue;                          // k_open_columns
+      odd_node<P, MACRO, MRT>(g, c, A, mac, x, y);
+    }
+    return;
+  }
+  if (__all_sync(0xffffffffu, flagged)) return;               // the whole span is band segments
+  odd_vec<P, MACRO, MRT>(g, c, A, mac, x0, y, lane, flagged);
+}
+
+// ------------------------------------------------------------------ open sides
+// Extrapolation sides (IBM_BC_INLET_NEE / IBM_BC_OUTLET_NEE): one thread
+// streams row y of side `side` (0: -x inlet, 1: +x outlet), the boundary
+// node x_b and its inner neighbour x_f.  It reads x_f's post-stream
+// populations, rebuilds the whole state of x_b as
+//   f_i(x_b) = f_i^eq(rho_b, u_b) + [f_i(x_f) - f_i^eq(rho(x_f), u(x_f))]
+// (inlet: u_b = U_in, rho_b = rho(x_f); outlet: rho_b = rho0, u_b = u(x_f)),
+// collides both nodes and stores their post-collision populations where
+// this step kind keeps them.  In the AA pattern the pair's slots belong to
+// the pair, so the other work of the step never touches them.
+template <int P, int PAR, bool MACRO, bool MRT>
+__device__ __forceinline__ void open_column(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
+                                            typename Prec<P>::S* __restrict__ A,
+                                            typename Prec<P>::R* __restrict__ mac, int side, int y) {
+  typedef typename Prec<P>::R R;
+  if (g.bc[side] != (side == 0 ? BC_INLET_NEE : BC_OUTLET_NEE)) return;
+  const int xb = side == 0 ? 0 : g.nx - 1, xf = side == 0 ? 1 : g.nx - 2;
+  R pf[9], pb[9], ps[2][9];
+  long long where;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) pf[i] = post_stream<P>(g, c, A, PAR, xf, y, i, where);
+  R rf, jxf, jyf;
+  moments9<R>(pf, rf, jxf, jyf);
+  const R inv = R(1) / rf;
+  const R uxf = jxf * inv, uyf = jyf * inv;
+  const R rb = side == 0 ? rf : c.rho0;
+  const R uxb = side == 0 ? c.inlet_u[0] : uxf, uyb = side == 0 ? c.inlet_u[1] : uyf;
+  const R jxb = rb * uxb, jyb = rb * uyb;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    pb[i] = feq_i<R>(i, rb, jxb, jyb, jxb * uxb, jxb * uyb, jyb * uyb) +
+            (pf[i] - feq_i<R>(i, rf, jxf, jyf, jxf * uxf, jxf * uyf, jyf * uyf));
+  const long long nn = (long long)g.nx * g.ny;
+  {
+    R rho, jx, jy;
+    collide_full<P, MRT>(pb, ps[0], rho, jx, jy, c);
+    if (MACRO) write_macro<R>(mac, nn, (long long)y * g.nx + xb, rho, jx, jy);
+    collide_full<P, MRT>(pf, ps[1], rho, jx, jy, c);
+    if (MACRO) write_macro<R>(mac, nn, (long long)y * g.nx + xf, rho, jx, jy);
+  }
+  for (int q = 0; q < 2; ++q) {
+    const int x = q == 0 ? xb : xf;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      if (PAR == 0) {                                      // even step: node-local
+        A[slot_index(g, opp(j), x, y)] = Prec<P>::st(ps[q][j], opp(j));
+      } else {
+        OddTargets o = oddTargets(g, x, y, j);
+        R v = ps[q][j];
+        if (o.wside >= 0) v -= c.wall[o.wside][j];
+        for (int k = 0; k < o.n; ++k) A[slot_index(g, o.slot[k], o.tx[k], o.ty[k])] = Prec<P>::st(v, o.slot[k]);
+      }
+    }
+  }
+}
+
 }  // namespace ibm

@@ -18,6 +18,8 @@
 // with immersed markers is split into the row segments without band nodes
 // (launched while the correction loop runs on another stream: the loop only
 // touches band-node slots) and the band segments (launched after it).
+#include <algorithm>
+
 #include "ibm_internal.h"
 #include "ibm_k1.cuh"
 
@@ -49,41 +51,8 @@ __global__ void __launch_bounds__(kK1Threads, k1_min_blocks(P, PAR)) k_collide_s
                                                         typename Prec<P>::S* __restrict__ A,
                                                         typename Prec<P>::R* __restrict__ mac,
                                                         const int* __restrict__ segflag, int nseg_x) {
-  constexpr int VEC = PAR ? VecTraits<P>::VEC_ODD : VecTraits<P>::VEC;
-  const int lane = threadIdx.x & 31;
-  const int y = blockIdx.y;
-  const int xw = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * VEC);
-  if (xw >= g.nx) return;                               // whole warp
-  const int x0 = xw + lane * VEC;
-  const bool flagged = MODE == K1_MAIN && x0 < g.nx && segflag[y * nseg_x + x0 / kSegW] != 0;
-  if (PAR == 0) {
-    if (flagged || x0 >= g.nx) return;
-    const bool nee = has_nee(g) && (nee_column(g, x0) || nee_column(g, min(x0 + VEC, g.nx) - 1));
-    if (x0 + VEC <= g.nx && !nee) {
-      even_vec<P, MACRO, MRT>(g, c, A, mac, x0, y);
-    } else {
-      for (int x = x0; x < g.nx && x < x0 + VEC; ++x)
-        if (!nee_column(g, x)) even_node<P, MACRO, MRT>(g, c, A, mac, x, y);
-    }
-    return;
-  }
-  const bool closed_x = g.bc[0] != BC_PERIODIC;
-  const int x_special =
-      closed_x ? ((g.bc[1] == BC_OUTLET || g.bc[1] == BC_OUTLET_NEE) ? g.nx - 2 : g.nx - 1) : g.nx;
-  const bool edge = (g.bc[2] != BC_PERIODIC && (y == 0 || y == g.ny - 1)) ||
-                    (closed_x && xw == 0) || (xw + 32 * VEC > x_special) || (xw + 32 * VEC > g.nx);
-  if (edge) {
-    for (int k = 0; k < VEC; ++k) {
-      const int x = x0 + k;
-      if (x >= g.nx) break;
-      if (MODE == K1_MAIN && segflag[y * nseg_x + x / kSegW]) continue;
-      if (nee_column(g, x)) continue;                          // k_open_columns
-      odd_node<P, MACRO, MRT>(g, c, A, mac, x, y);
-    }
-    return;
-  }
-  if (__all_sync(0xffffffffu, flagged)) return;               // the whole span is band segments
-  odd_vec<P, MACRO, MRT>(g, c, A, mac, x0, y, lane, flagged);
+  k1_span<P, PAR, MACRO, MODE, MRT>(g, c, A, mac, segflag, nseg_x, blockIdx.y,
+                                    (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------------ fields
@@ -168,6 +137,25 @@ __global__ void k_macro_to_double(long long n, const R* __restrict__ mac, double
   if (k < n) out[k] = (double)mac[k];
 }
 
+// NaN/Inf watchdog: every stored population of the lattice (padding columns
+// excluded) is checked; one bit in the error word records a non-finite value.
+template <int P>
+__global__ void k_watchdog(Geom g, const typename Prec<P>::S* __restrict__ A, int* __restrict__ ctr) {
+  typedef typename Prec<P>::R R;
+  const long long n = (long long)g.ny * g.nx;
+  bool bad = false;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long y = k / g.nx, x = k - y * g.nx;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const R v = Prec<P>::ld(A[i * g.plane + y * g.nxp + x], i);
+      bad |= !isfinite(v);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr[CTR_ERR], ERR_DIVERGED);
+}
+
 // ------------------------------------------------------------------ launchers
 static dim3 row_grid(const Geom& g, int bs) { return dim3((g.nx + bs - 1) / bs, g.ny); }
 
@@ -201,49 +189,10 @@ static void launch_k1(const Ctx& h, const StepConsts<typename Prec<P>::R>& c, in
 template <int P, int PAR, bool MACRO, bool MRT>
 __global__ void k_open_columns(Geom g, StepConsts<typename Prec<P>::R> c, typename Prec<P>::S* __restrict__ A,
                                typename Prec<P>::R* __restrict__ mac) {
-  typedef typename Prec<P>::R R;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * g.ny) return;
-  const int side = t / g.ny, y = t - side * g.ny;          // side 0: -x (inlet), 1: +x (outlet)
-  if (g.bc[side] != (side == 0 ? BC_INLET_NEE : BC_OUTLET_NEE)) return;
-  const int xb = side == 0 ? 0 : g.nx - 1, xf = side == 0 ? 1 : g.nx - 2;
-  R pf[9], pb[9], ps[2][9];
-  long long where;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) pf[i] = post_stream<P>(g, c, A, PAR, xf, y, i, where);
-  R rf, jxf, jyf;
-  moments9<R>(pf, rf, jxf, jyf);
-  const R inv = R(1) / rf;
-  const R uxf = jxf * inv, uyf = jyf * inv;
-  const R rb = side == 0 ? rf : c.rho0;
-  const R uxb = side == 0 ? c.inlet_u[0] : uxf, uyb = side == 0 ? c.inlet_u[1] : uyf;
-  const R jxb = rb * uxb, jyb = rb * uyb;
-#pragma unroll
-  for (int i = 0; i < 9; ++i)
-    pb[i] = feq_i<R>(i, rb, jxb, jyb, jxb * uxb, jxb * uyb, jyb * uyb) +
-            (pf[i] - feq_i<R>(i, rf, jxf, jyf, jxf * uxf, jxf * uyf, jyf * uyf));
-  const long long nn = (long long)g.nx * g.ny;
-  {
-    R rho, jx, jy;
-    collide_full<P, MRT>(pb, ps[0], rho, jx, jy, c);
-    if (MACRO) write_macro<R>(mac, nn, (long long)y * g.nx + xb, rho, jx, jy);
-    collide_full<P, MRT>(pf, ps[1], rho, jx, jy, c);
-    if (MACRO) write_macro<R>(mac, nn, (long long)y * g.nx + xf, rho, jx, jy);
-  }
-  for (int q = 0; q < 2; ++q) {
-    const int x = q == 0 ? xb : xf;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      if (PAR == 0) {                                      // even step: node-local
-        A[slot_index(g, opp(j), x, y)] = Prec<P>::st(ps[q][j], opp(j));
-      } else {
-        OddTargets o = oddTargets(g, x, y, j);
-        R v = ps[q][j];
-        if (o.wside >= 0) v -= c.wall[o.wside][j];
-        for (int k = 0; k < o.n; ++k) A[slot_index(g, o.slot[k], o.tx[k], o.ty[k])] = Prec<P>::st(v, o.slot[k]);
-      }
-    }
-  }
+  const int side = t / g.ny;
+  open_column<P, PAR, MACRO, MRT>(g, c, A, mac, side, t - side * g.ny);
 }
 
 template <int P, int PAR, bool MACRO>
@@ -317,6 +266,20 @@ static void launch_fields_t(const Ctx& h, int op, const double* dev_in, double* 
     case FIELD_OP_MACRO_OUT:
       k_macro_to_double<R><<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(3 * n, mac, dev_out);
       break;
+  }
+}
+
+void launch_watchdog(const Ctx& h, cudaStream_t s) {
+  const long long n = (long long)h.geom.nx * h.geom.ny;
+  const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 4LL * h.ib_grid_max);
+  switch (h.prec) {
+    case PREC_FP64: k_watchdog<PREC_FP64><<<blocks, 256, 0, s>>>(h.geom, (const double*)h.f, h.dctr); break;
+    case PREC_FP32: k_watchdog<PREC_FP32><<<blocks, 256, 0, s>>>(h.geom, (const float*)h.f, h.dctr); break;
+    case PREC_FP16_DEV:
+      k_watchdog<PREC_FP16_DEV><<<blocks, 256, 0, s>>>(h.geom, (const __half*)h.f, h.dctr);
+      break;
+    default:
+      k_watchdog<PREC_BF16_DEV><<<blocks, 256, 0, s>>>(h.geom, (const __nv_bfloat16*)h.f, h.dctr);
   }
 }
 

@@ -45,15 +45,21 @@ cudaError_t scratch_base(int dev, void** out) {
   return cudaSuccess;
 }
 
-// Bump allocator over the scratch array (256-byte aligned pieces).
+// Bump allocator over the scratch array (256-byte aligned pieces).  A piece
+// that does not fit fails every later take as well (ok stays false), so one
+// check after the last take covers them all.
 struct Carve {
   unsigned char* base;
   size_t used;
   size_t cap;
+  bool ok = true;
   template <class T>
   T* take(size_t count) {
     const size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
-    if (used + bytes > cap) return nullptr;
+    if (!ok || used + bytes > cap) {
+      ok = false;
+      return nullptr;
+    }
     T* p = reinterpret_cast<T*>(base + used);
     used += bytes;
     return p;
@@ -121,6 +127,9 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
     return na_fail(IBM_ERR_INVALID, "ibm_ib_correct_noalloc: prec must be IBM_FP64 or IBM_FP32");
   if (!f || !xy || !ds || !uvel)
     return na_fail(IBM_ERR_INVALID, "ibm_ib_correct_noalloc: f, xy, ds and uvel are required");
+  // CUDA keeps one pending launch error per host thread: clear what earlier
+  // work left there, so that the checks below see only this call's work.
+  cudaGetLastError();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
     cudaGetLastError();
@@ -167,7 +176,11 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
   c.bcap = n_markers * kStencil;
   c.nseg_x = (nx + kSegW - 1) / kSegW;
   c.segcap = c.bcap;
-  c.ib_grid = sms;
+  // At most 512 markers: the correction kernel runs as one CTA with block
+  // barriers (as ibm_step does for boundaries this small), so it never waits
+  // for CTAs that other work on the device keeps from being scheduled.
+  c.ib_grid = 1;
+  c.ib_grid_last = 1;
   c.ib_grid_max = sms;
   c.ib_prio = 0;
   c.band_collide = false;                   // correction only
@@ -204,18 +217,22 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
   c.dresid = cv.take<unsigned char>(R * (n_corr + 1));
   c.dbodies = cv.take<BodyDev>(1);
   c.dfpart = cv.take<double>((size_t)((n_markers + kForceChunk - 1) / kForceChunk) * 3);
-  if (!c.dfpart)
+  if (!cv.ok)
     return na_fail(IBM_ERR_INVALID, "ibm_ib_correct_noalloc: the scratch array is too small for this call");
 
   // The scratch array keeps the previous call's contents: reset what the
   // kernels expect to start empty.
-  cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)nodes, s);
-  cudaMemsetAsync(c.dsegflag, 0, sizeof(int) * (size_t)c.nseg_x * ny, s);
-  cudaMemsetAsync(c.dctr, 0, sizeof(int) * CTR_COUNT, s);
-  cudaMemsetAsync(c.dbar, 0, sizeof(unsigned long long), s);
-  cudaMemsetAsync(c.dbcnt, 0, sizeof(int) * (size_t)c.bcap, s);
-  cudaMemsetAsync(c.dent, 0, ent_bytes * (size_t)c.bcap * kBandCap, s);
-  cudaMemsetAsync(c.dG, 0, ent_bytes * (size_t)n_markers * kGCap, s);
+  e = cudaMemsetAsync(c.dnode2band, 0xFF, sizeof(int) * (size_t)nodes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.dsegflag, 0, sizeof(int) * (size_t)c.nseg_x * ny, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.dctr, 0, sizeof(int) * CTR_COUNT, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.dbar, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.dbcnt, 0, sizeof(int) * (size_t)c.bcap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.dent, 0, ent_bytes * (size_t)c.bcap * kBandCap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.dG, 0, ent_bytes * (size_t)n_markers * kGCap, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return na_fail(IBM_ERR_CUDA, std::string("ibm_ib_correct_noalloc: ") + cudaGetErrorString(e));
+  }
   if (prec == IBM_FP64)
     k_na_prepare<double><<<(n_markers + 127) / 128, 128, 0, s>>>(n_markers, xy, ds, uvel, c.dX, c.dY, c.dds,
         c.ddX, c.ddY, c.dmbody, (double*)c.dUx, (double*)c.dUy, c.dbodies);
@@ -228,17 +245,17 @@ extern "C" ibm_status ibm_ib_correct_noalloc(int nx, int ny, int prec, void* f, 
     k_na_finish<double><<<1, 128, 0, s>>>(n_corr + 1, (const double*)c.dresid, c.dbodies, resid_out, force_out);
   else
     k_na_finish<float><<<1, 128, 0, s>>>(n_corr + 1, (const float*)c.dresid, c.dbodies, resid_out, force_out);
+  e = cudaGetLastError();                   // launch errors of this call's kernels
   int ctr[CTR_COUNT] = {0, 0, 0, 0};
-  cudaMemcpyAsync(ctr, c.dctr, sizeof(ctr), cudaMemcpyDeviceToHost, s);
-  e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctr, c.dctr, sizeof(ctr), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return na_fail(IBM_ERR_CUDA, std::string("ibm_ib_correct_noalloc: ") + cudaGetErrorString(e));
   }
-  if (ctr[CTR_ERR] & ERR_BARRIER)
-    return na_fail(IBM_ERR_TIMEOUT, "ibm_ib_correct_noalloc: the correction-loop grid barrier timed out");
-  if (ctr[CTR_ERR])
+  if (ctr[CTR_ERR] & ERR_DIVERGED)
+    return na_fail(IBM_ERR_DIVERGED, "ibm_ib_correct_noalloc: non-finite no-slip residual");
+  if (ctr[CTR_ERR] & (ERR_BAND_CAP | ERR_LIST_CAP | ERR_SEG_CAP | ERR_G_CAP))
     return na_fail(IBM_ERR_BOUNDS, "ibm_ib_correct_noalloc: markers too dense for the band capacity");
   return IBM_OK;
 }

@@ -46,8 +46,10 @@ SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields
            "ibm_abi_version", "ibm_ib_correct_noalloc", "ibm_set_option",
            "ibm_server_create", "ibm_server_submit", "ibm_server_progress", "ibm_server_wait",
            "ibm_server_result", "ibm_server_release", "ibm_server_get_stats", "ibm_server_destroy",
-           "ibm_server_last_error", "ibm_set_marker_velocities", "ibm_autotune_ib")
+           "ibm_server_last_error", "ibm_set_marker_velocities", "ibm_autotune_ib",
+           "ibm_server_autotune")
 IBM_OPT_IB_CTAS, IBM_OPT_IB_THREADS = 1, 2
+IBM_OPT_WATCHDOG_STEPS, IBM_OPT_BARRIER_LIMIT_US, IBM_OPT_TEST_DROP_ARRIVAL = 3, 4, 5
 OUT_MACRO, OUT_BODIES, OUT_RESIDUAL = 1, 2, 4
 
 
@@ -78,7 +80,8 @@ class BodyDesc(ctypes.Structure):
 class ServerDesc(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_device_bytes", ctypes.c_double),
                 ("max_active", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
-                ("ib_cta_budget", ctypes.c_int), ("ib_markers_per_cta", ctypes.c_int)]
+                ("ib_cta_budget", ctypes.c_int), ("ib_markers_per_cta", ctypes.c_int),
+                ("batched", ctypes.c_int), ("tile_nodes", ctypes.c_int), ("corr_first", ctypes.c_int)]
 
 
 class CaseDesc(ctypes.Structure):
@@ -156,6 +159,9 @@ def load(build_if_missing: bool = True):
         lib.ibm_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         lib.ibm_server_destroy.argtypes = [vp]
         lib.ibm_server_last_error.argtypes = [vp]
+        lib.ibm_server_autotune.argtypes = [vp, ctypes.POINTER(CaseDesc), ci, ctypes.POINTER(ci), ci,
+                                            ctypes.POINTER(ci), ci, ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                            ctypes.POINTER(ci), _D]
         lib.ibm_server_last_error.restype = ctypes.c_char_p
         for name in SYMBOLS:
             if name not in ("ibm_last_error", "ibm_abi_version", "ibm_server_last_error"):
@@ -363,9 +369,10 @@ def _scheck(st: int, srv, where: str) -> int:
 
 
 def ibm_server_create(device=0, max_device_bytes=0.0, max_active=32, steps_per_launch=16,
-                      ib_cta_budget=0, ib_markers_per_cta=0):
+                      ib_cta_budget=0, ib_markers_per_cta=0, batched=False, tile_nodes=0, corr_first=0):
     d = ServerDesc(int(device), float(max_device_bytes), int(max_active), int(steps_per_launch),
-                   int(ib_cta_budget), int(ib_markers_per_cta))
+                   int(ib_cta_budget), int(ib_markers_per_cta), int(bool(batched)), int(tile_nodes),
+                   int(corr_first))
     srv = ctypes.c_void_p()
     _scheck(load().ibm_server_create(ctypes.byref(d), ctypes.byref(srv)), None, "ibm_server_create")
     return srv
@@ -402,8 +409,9 @@ def _body_desc(b) -> BodyDesc:
     return bd
 
 
-def ibm_server_submit(srv, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BODIES | OUT_RESIDUAL) -> int:
-    """Submit a workloads.Case for nsteps time steps; returns its id."""
+def _case_desc_of(case, nsteps, prec, outputs):
+    """A CaseDesc for a workloads.Case and the arrays it points to (keep them
+    alive while the descriptor is used)."""
     c = CaseDesc()
     c.lattice = _lattice_desc(case.nx, case.ny, case.tau, case.rho0, prec, case.bc, case.wall_u,
                               case.inlet_u, case.n_corr, mrt=case.mrt, delta_points=case.delta_points)
@@ -419,9 +427,36 @@ def ibm_server_submit(srv, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BO
     c.ds = ds.ctypes.data_as(_D)
     c.nsteps = int(nsteps)
     c.outputs = int(outputs)
+    return c, (bodies, nmark, xy, ds)
+
+
+def ibm_server_submit(srv, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BODIES | OUT_RESIDUAL) -> int:
+    """Submit a workloads.Case for nsteps time steps; returns its id."""
+    c, keep = _case_desc_of(case, nsteps, prec, outputs)
     cid = ctypes.c_longlong()
     _scheck(load().ibm_server_submit(srv, ctypes.byref(c), ctypes.byref(cid)), srv, "ibm_server_submit")
+    del keep
     return cid.value
+
+
+def ibm_server_autotune(srv, cases, nsteps, prec="fp32", tile_nodes=None, markers_per_cta=None):
+    """Batched mode's autotuner on sample cases (workloads.Case), each run for
+    nsteps steps; returns (tile_nodes, markers_per_cta, corr_first, seconds)."""
+    descs, keep = [], []
+    for case in cases:
+        c, k = _case_desc_of(case, nsteps, prec, OUT_RESIDUAL)
+        descs.append(c)
+        keep.append(k)
+    arr = (CaseDesc * len(descs))(*descs)
+    tl = list(tile_nodes or [])
+    ml = list(markers_per_cta or [])
+    ta = (ctypes.c_int * max(len(tl), 1))(*tl)
+    ma = (ctypes.c_int * max(len(ml), 1))(*ml)
+    bt, bm, bo, sec = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _scheck(load().ibm_server_autotune(srv, arr, len(descs), ta, len(tl), ma, len(ml), ctypes.byref(bt),
+                                       ctypes.byref(bm), ctypes.byref(bo), ctypes.byref(sec)),
+            srv, "ibm_server_autotune")
+    return bt.value, bm.value, bo.value, sec.value
 
 
 def ibm_server_progress(srv) -> int:
@@ -465,10 +500,15 @@ class Server:
     """Owning wrapper of an ibm_server (context manager)."""
 
     def __init__(self, device=0, max_device_bytes=0.0, max_active=32, steps_per_launch=16,
-                 ib_cta_budget=0, ib_markers_per_cta=0):
+                 ib_cta_budget=0, ib_markers_per_cta=0, batched=False, tile_nodes=0, corr_first=0):
         self.s = ibm_server_create(device, max_device_bytes, max_active, steps_per_launch, ib_cta_budget,
-                                   ib_markers_per_cta)
+                                   ib_markers_per_cta, batched, tile_nodes, corr_first)
         self._shapes = {}
+
+    def autotune(self, cases, nsteps, prec="fp32", tile_nodes=None, markers_per_cta=None):
+        """Batched mode: time the candidate settings on sample cases and keep
+        the fastest; returns (tile_nodes, markers_per_cta, corr_first, s)."""
+        return ibm_server_autotune(self.s, cases, nsteps, prec, tile_nodes, markers_per_cta)
 
     def submit(self, case, nsteps, prec="fp32", outputs=OUT_MACRO | OUT_BODIES | OUT_RESIDUAL) -> int:
         cid = ibm_server_submit(self.s, case, nsteps, prec, outputs)

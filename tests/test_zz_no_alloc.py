@@ -24,10 +24,11 @@ EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=np.float64)
 EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=np.float64)
 
 
-def _case_inputs(case, seed):
+def _case_inputs(case, seed, prec):
     """Initial populations (an equilibrium of seeded random fields, set on a
-    handle) and the flattened marker arrays of every body of the case."""
-    h = ibm.Lattice(case.nx, case.ny, case.tau, prec="fp64", n_corr=case.n_corr)
+    handle of the given precision, so that they are representable in it) and
+    the flattened marker arrays of every body of the case."""
+    h = ibm.Lattice(case.nx, case.ny, case.tau, prec=prec, n_corr=case.n_corr)
     rho, ux, uy = wl.random_fields(case.nx, case.ny, seed, du=0.01, drho=0.005)
     h.init_equilibrium(rho, ux, uy)
     f0 = h.f
@@ -42,10 +43,10 @@ def _case_inputs(case, seed):
     return f0, xy, ds, np.concatenate(uv)
 
 
-def _regular_path(case, f0):
+def _regular_path(case, f0, prec):
     """One ibm_step from f0: the residual history, the summed body force and
     the moments of the corrected state (before the collision)."""
-    lat = ibm.Lattice.from_case(case, prec="fp64")
+    lat = ibm.Lattice.from_case(case, prec=prec)
     lat.f = f0
     lat.step(1)
     rho, ux, uy = lat.moments()
@@ -54,45 +55,56 @@ def _regular_path(case, f0):
     return out
 
 
-def _noalloc_path(case, f0, xy, ds, uv):
+def _noalloc_path(case, prec, f0, xy, ds, uv):
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", 0)
-    f = torch.from_numpy(np.ascontiguousarray(f0)).to(dev)
+    ftype = np.float64 if prec == "fp64" else np.float32
+    f = torch.from_numpy(np.ascontiguousarray(f0, dtype=ftype)).to(dev)
     dxy = torch.from_numpy(np.ascontiguousarray(xy)).to(dev)
     dds = torch.from_numpy(np.ascontiguousarray(ds)).to(dev)
     duv = torch.from_numpy(np.ascontiguousarray(uv)).to(dev)
     resid = torch.zeros(case.n_corr + 1, dtype=torch.float64, device=dev)
     force = torch.zeros(2, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
-    ibm.ibm_ib_correct_noalloc(case.nx, case.ny, "fp64", f.data_ptr(), xy.shape[0], dxy.data_ptr(),
+    ibm.ibm_ib_correct_noalloc(case.nx, case.ny, prec, f.data_ptr(), xy.shape[0], dxy.data_ptr(),
                                dds.data_ptr(), duv.data_ptr(), case.n_corr, resid.data_ptr(),
                                force.data_ptr(), None)
     fc = f.cpu().numpy()
-    rho = fc.sum(axis=0)
-    ux = np.tensordot(EX, fc, axes=1) / rho
-    uy = np.tensordot(EY, fc, axes=1) / rho
+    fd = fc.astype(np.float64)
+    rho = fd.sum(axis=0)
+    ux = np.tensordot(EX, fd, axes=1) / rho
+    uy = np.tensordot(EY, fd, axes=1) / rho
     return dict(resid=resid.cpu().numpy(), force=force.cpu().numpy(), rho=rho, ux=ux, uy=uy), fc
 
 
-def _compare(a, b):
-    # the tolerances of the FP64 parity tests
-    assert relerr(a["rho"], b["rho"]) < 1e-12
-    assert relerr(a["ux"], b["ux"]) < 1e-12
-    assert relerr(a["uy"], b["uy"]) < 1e-12
-    assert relerr(a["resid"], b["resid"]) < 1e-10
-    assert relerr(a["force"], b["force"]) < 1e-10
+def _compare(a, b, prec):
+    if prec == "fp64":
+        # the tolerances of the FP64 parity tests
+        tol, tol_r = 1e-12, 1e-10
+    else:
+        # the regular path forms rho and u in float from the same corrected
+        # float populations that are summed here in double: rounding of the
+        # moments only (~1e-7 of their scale); the residuals and the force
+        # come from the same kernels on the same data
+        tol, tol_r = 1e-5, 1e-6
+    assert relerr(a["rho"], b["rho"]) < tol
+    assert relerr(a["ux"], b["ux"]) < tol
+    assert relerr(a["uy"], b["uy"]) < tol
+    assert relerr(a["resid"], b["resid"]) < tol_r
+    assert relerr(a["force"], b["force"]) < tol_r
 
 
-def test_noalloc_matches_regular_path_on_two_calls_in_a_row():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_matches_regular_path_on_two_calls_in_a_row(prec):
     first = wl.couette_64()
     second = wl.couette(48, n_corr=7)
-    in1 = _case_inputs(first, seed=5)
-    in2 = _case_inputs(second, seed=6)
-    got1, f1 = _noalloc_path(first, *in1)
-    got2, _ = _noalloc_path(second, *in2)
-    _compare(got1, _regular_path(first, in1[0]))
-    _compare(got2, _regular_path(second, in2[0]))
-    again, f1b = _noalloc_path(first, *in1)
+    in1 = _case_inputs(first, 5, prec)
+    in2 = _case_inputs(second, 6, prec)
+    got1, f1 = _noalloc_path(first, prec, *in1)
+    got2, _ = _noalloc_path(second, prec, *in2)
+    _compare(got1, _regular_path(first, in1[0], prec), prec)
+    _compare(got2, _regular_path(second, in2[0], prec), prec)
+    again, f1b = _noalloc_path(first, prec, *in1)
     assert np.array_equal(f1, f1b)
     assert np.array_equal(got1["resid"], again["resid"])
 
