@@ -49,8 +49,12 @@ def parse():
     p.add_argument("--n-corr", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--cpu-budget", type=float, default=20.0,
-                   help="seconds of oracle work for the cpu_baseline sample")
+    p.add_argument("--cpu-budget", type=float, default=12.0,
+                   help="seconds of oracle work for each cpu_baseline sample (one thread, all cores)")
+    p.add_argument("--cpu-sample-set", action="store_true",
+                   help="also time the oracle on the 64^2 ring case in full (5000 steps), the 1024^2 "
+                        "and 4096^2 Couette lattices and the 1600x800 cylinder for 100 steps each, "
+                        "one thread and all cores (minutes of host time)")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--ib-ctas", type=int, default=0,
                    help="CTAs of the correction kernel (0: the library's choice)")
@@ -58,8 +62,9 @@ def parse():
                    help="keep the library's default correction grid instead of timing candidates")
     p.add_argument("--ib-threads", type=int, default=0,
                    help="threads per correction-kernel CTA (0: the library's choice)")
-    p.add_argument("--serve-requests", type=int, default=64)
+    p.add_argument("--serve-requests", type=int, default=512)
     p.add_argument("--serve-steps", type=int, default=500)
+    p.add_argument("--serve-prec", choices=list(BYTES_PER_POP), default="fp32")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
     p.add_argument("--serve-active", type=int, default=32, help="cases resident at once")
     return p.parse_args()
@@ -144,13 +149,40 @@ def measured_peak_hbm():
 
 
 # ---------------------------------------------------------------- oracle timing
-def time_oracle(n: int, steps: int, n_corr: int):
+def host_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.startswith("Model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count() or 1, "cpu_model": model or "unknown"}
+
+
+def oracle_lattice(case, threaded):
     import oracle
-    from paper_1803_09380_gb300 import workloads as wl
-    case = wl.couette(n, n_corr=n_corr)
-    L = oracle.Lattice(case.nx, case.ny, case.tau, n_corr=case.n_corr)
+    L = oracle.Lattice(case.nx, case.ny, case.tau, rho0=case.rho0, bc=case.bc, wall_u=case.wall_u,
+                       inlet_u=case.inlet_u, n_corr=case.n_corr, mrt=case.mrt, threaded=threaded)
     for b in case.bodies:
         L.add_body(b.xy, b.ds, **b.as_kwargs())
+    return L
+
+
+def time_oracle(case, steps: int, threaded: bool) -> float:
+    L = oracle_lattice(case, threaded)
     t = time.perf_counter()
     L.step(steps)
     dt = time.perf_counter() - t
@@ -158,51 +190,98 @@ def time_oracle(n: int, steps: int, n_corr: int):
     return dt
 
 
-def oracle_sample(budget_s: float, n_max: int, n_corr: int, steps_hint: int = 1):
+def oracle_threads(threaded: bool) -> int:
+    import oracle
+    return oracle.set_threads(0) if threaded else 1
+
+
+def oracle_sample(budget_s: float, n_max: int, n_corr: int, threaded: bool):
     """Pick the largest Couette size (<= n_max, halving) whose oracle step
     fits the budget, from a calibration on 128^2; returns (n, steps)."""
-    per_node = time_oracle(128, 2, n_corr) / (2 * 128 * 128)
+    from paper_1803_09380_gb300 import workloads as wl
+    per_node = time_oracle(wl.couette(128, n_corr=n_corr), 2, threaded) / (2 * 128 * 128)
     n = n_max
-    while n > 64 and per_node * n * n * steps_hint > budget_s:
+    while n > 64 and per_node * n * n > budget_s:
         n //= 2
     steps = max(1, int(budget_s / (per_node * n * n)))
     return n, min(steps, 1000)
 
 
 def cpu_baseline(args):
-    n, steps = oracle_sample(args.cpu_budget, args.n, args.n_corr)
-    dt = time_oracle(n, steps, args.n_corr)
-    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, one thread, Couette {n}x{n} (same geometry scaled), "
-                      f"{steps} step(s), {args.n_corr} correction iterations, {dt:.1f} s"}
+    """The oracle as it stands on a bounded sample of the workload (the same
+    geometry scaled down until a step fits the budget): all host cores (the
+    -fopenmp build; the reported value) and one thread."""
+    import oracle
+    from paper_1803_09380_gb300 import workloads as wl
+    info = host_info()
+    runs = {}
+    for threaded in ([False, True] if oracle.threaded_available() else [False]):
+        n, steps = oracle_sample(args.cpu_budget, args.n, args.n_corr, threaded)
+        dt = time_oracle(wl.couette(n, n_corr=args.n_corr), steps, threaded)
+        runs[threaded] = {"value": n * n * steps / dt / 1e6, "cores": oracle_threads(threaded),
+                          "sample": f"Couette {n}x{n} (same geometry scaled), {steps} step(s), {dt:.1f} s"}
+    best = runs.get(True, runs[False])
+    out = {"value": best["value"], "unit": "MLUPS", "cores": best["cores"], "kind": "oracle",
+           "sample": f"FP64 C oracle, {best['cores']} thread(s), {best['sample']}, "
+                     f"{args.n_corr} correction iterations",
+           "single_thread": {"value": runs[False]["value"], "sample": runs[False]["sample"]}}
+    out.update(info)
+    if args.cpu_sample_set:
+        out["sample_set"] = cpu_sample_set(args)
+    return out
+
+
+def cpu_sample_set(args):
+    """The oracle on the survey's sample set, one thread and all cores."""
+    import oracle
+    from paper_1803_09380_gb300 import workloads as wl
+    cases = [("ring 64x64 (radii 10, 25), 5000 steps", wl.couette_64(), 5000),
+             ("Couette 1024x1024, 100 steps", wl.couette(1024, n_corr=args.n_corr), 100),
+             ("Couette 4096x4096, 100 steps", wl.couette(4096, n_corr=args.n_corr), 100),
+             ("cylinder 1600x800 (D 40, 126 markers, Re 20), 100 steps",
+              wl.cylinder(nx=1600, ny=800, diameter=40.0, center=(400.0, 400.0), u_in=0.05, re=20.0,
+                          markers=126), 100)]
+    out = []
+    for name, case, steps in cases:
+        rec = {"case": name}
+        for threaded in ([False, True] if oracle.threaded_available() else [False]):
+            dt = time_oracle(case, steps, threaded)
+            key = f"mlups_{oracle_threads(threaded)}_threads" if threaded else "mlups_1_thread"
+            rec[key] = case.nx * case.ny * steps / dt / 1e6
+        out.append(rec)
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle as it stands, timed like our arm: W untimed steps, then K
+    timed steps, each one time step of the workload's geometry scaled down
+    so that the whole run ends within minutes, on all host cores."""
     if rank != 0:
         return
+    import oracle
     from paper_1803_09380_gb300 import workloads as wl
     case = wl.couette(args.n, n_corr=args.n_corr)
+    threaded = oracle.threaded_available()
     total = args.steps + args.warmup
-    n, _ = oracle_sample(150.0 / max(total, 1), args.n, args.n_corr)
-    import oracle
-    c = wl.couette(n, n_corr=args.n_corr)
-    L = oracle.Lattice(c.nx, c.ny, c.tau, n_corr=c.n_corr)
-    for b in c.bodies:
-        L.add_body(b.xy, b.ds, **b.as_kwargs())
+    n, _ = oracle_sample(150.0 / max(total, 1), args.n, args.n_corr, threaded)
+    L = oracle_lattice(wl.couette(n, n_corr=args.n_corr), threaded)
     L.step(args.warmup)
     t = time.perf_counter()
     L.step(args.steps)
     dt = time.perf_counter() - t
     value = n * n * args.steps / dt / 1e6
-    sample = (f"FP64 C oracle, one thread; each step one time step of the Couette lattice "
+    cores = oracle_threads(threaded)
+    sample = (f"FP64 C oracle, {cores} thread(s); each step one time step of the Couette lattice "
               f"scaled to {n}x{n} (same geometry, {args.n_corr} correction iterations)")
+    cfg = workload_config(args, case)
+    cfg["timed_sample"] = f"{n}x{n} lattice, FP64 oracle"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args, case),
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": dict({"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                  "sample": sample}, **host_info()),
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -211,11 +290,11 @@ def run_reference(args, rank, world):
 # DRAM bytes (read + write) per collide+stream launch from one ncu capture,
 # the mean of the two AA step kinds, with the sha256 prefix of the kernel
 # sources the capture ran; the figure is reported only while the sources
-# still hash to that value.  Sources: the summaries under profiles/.
+# still hash to that value.
 TRAFFIC = {
-    ("fp32", 4096): (1139.8e6, "62a14777a1211814", "profiles/k_collide_stream_fp32_couette4096.md"),
-    ("fp16", 4096): (542.8e6, "62a14777a1211814", "profiles/k_collide_stream_fp16_couette4096.md"),
-    ("fp64", 4096): (2314.4e6, "62a14777a1211814", "profiles/k_collide_stream_fp64_couette4096.md"),
+    ("fp32", 4096): (1139.8e6, "62a14777a1211814"),
+    ("fp16", 4096): (542.8e6, "62a14777a1211814"),
+    ("fp64", 4096): (2314.4e6, "62a14777a1211814"),
 }
 KERNEL_SOURCES = ("ibm_k1.cuh", "ibm_lbm.cu", "ibm_device.cuh")
 
@@ -234,7 +313,8 @@ def measured_traffic(prec: str, n: int):
     t = TRAFFIC.get((prec, n))
     if t is None or kernel_source_hash() != t[1]:
         return None, None
-    return t[0], t[2]
+    return t[0], (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of k_collide_stream, "
+                  f"mean of both step kinds, kernel sources sha256 {t[1]}")
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -313,9 +393,9 @@ def run_ours(args, rank, world, local_rank, dist):
     k1_avg_s = (k1_ms / max(k1_n, 1)) * 1e-3
     achieved = bytes_per_update * main_nodes / k1_avg_s / 1e9
     traffic, traffic_src = measured_traffic(args.prec, args.n)
-    limiter = {"fp64": "FP64 arithmetic (FP64 pipe 84 % active; profiles/k_collide_stream_fp64_couette4096.md)",
-               "fp16": "instruction issue (profiles/k_collide_stream_fp16_couette4096.md)",
-               "bf16": "instruction issue (profiles/k_collide_stream_fp16_couette4096.md)"}.get(args.prec)
+    limiter = {"fp64": "FP64 arithmetic (ncu: FP64 pipe 84 % active in k_collide_stream)",
+               "fp16": "instruction issue (ncu: issue slots busy in k_collide_stream)",
+               "bf16": "instruction issue (ncu: issue slots busy in k_collide_stream)"}.get(args.prec)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": "k_collide_stream (band-free row segments, both AA step kinds)",
@@ -346,8 +426,11 @@ def run_ours(args, rank, world, local_rank, dist):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": DTYPE[args.prec], "data": "synthetic",
-                "config": dict(workload_config(args, case),
-                               correction_ctas=tuned[0] if tuned else (args.ib_ctas or "library default")),
+                "config": workload_config(args, case),
+                "correction_ctas": tuned[0] if tuned else (args.ib_ctas or "library default"),
+                "timed_path": "ibm_step with IBM_STEP_TIME_KERNELS | IBM_STEP_NO_MACRO: every step "
+                              "corrects, collides and streams; rho and u are not written out on the "
+                              "last step of the call (the optional output fields)",
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "serving": serving}
         print(json.dumps(line), flush=True)
@@ -376,45 +459,76 @@ def k1_alone(args, local_rank, peak, bytes_per_update, steps=200):
 
 
 def run_serving(args, local_rank):
-    """Continuous batching on a bounded request stream with the serving mix
-    (seeded Poisson arrivals; a uniform mix of Couette with N log-uniform in
-    64-2048, fixed cylinders on 2ny x ny lattices with ny in 200-800 and Re
-    10-100, and one or two settling disks of D 10-30 in a 200 x 600 box),
-    FP32, `serve_steps` time steps per request, arrivals fast enough to keep
-    the server saturated.  The same requests then run one at a time through
-    the same API (max_active = 1)."""
+    """Continuous batching on the serving stream (512 requests with seeded
+    Poisson arrivals; a uniform mix of Couette with N log-uniform in 64-2048,
+    fixed cylinders on 2ny x ny lattices with ny in 200-800 and Re 10-100,
+    and one or two settling disks of D 10-30 in a 200 x 600 box),
+    `serve_steps` time steps per request, arrivals fast enough to keep the
+    server saturated.  Two one-at-a-time baselines run the same requests at
+    the same precision, so every solve has the same result and accuracy:
+    each case as its own ibm.Lattice (the library's default correction grid,
+    graph replays of 8-step blocks), one after another; and the same server
+    with one slot."""
     from paper_1803_09380_gb300 import ibm
     from paper_1803_09380_gb300 import workloads as wl
     stream = wl.serving_stream(n_requests=args.serve_requests, seed=1803, rate_hz=args.serve_rate,
                                steps=args.serve_steps)
-    out = {"requests": len(stream), "steps_per_request": args.serve_steps, "precision": "fp32",
+    prec = args.serve_prec
+    out = {"requests": len(stream), "steps_per_request": args.serve_steps, "precision": prec,
            "mix": "Couette N 64-2048 log-uniform, cylinder 2ny x ny (ny 200-800, Re 10-100), "
                   f"1-2 settling disks D 10-30 in 200x600; Poisson arrivals at {args.serve_rate:g}/s, "
-                  "seed 1803"}
+                  "seed 1803",
+           "solve": f"{args.serve_steps} time steps of the case, residual history read back"}
 
-    def serve(max_active, paced):
-        with ibm.Server(device=local_rank, max_active=max_active, steps_per_launch=16) as srv:
+    def serve(max_active, paced, batched=False, tune=False):
+        with ibm.Server(device=local_rank, max_active=max_active, steps_per_launch=16,
+                        batched=batched) as srv:
+            tuned = None
+            if tune:
+                # the autotuner times tile size, markers per correction CTA and
+                # task order on the stream's first 24 requests (64 steps each)
+                t, m, o, _ = srv.autotune([c for _, c, _ in stream[:24]], 64, prec=prec)
+                tuned = {"tile_nodes": t, "markers_per_cta": m, "corr_first": o}
             t0 = time.perf_counter()
             k = 0
             while k < len(stream):
                 if paced:
                     while k < len(stream) and stream[k][0] > time.perf_counter() - t0:
                         srv.progress()
-                srv.submit(stream[k][1], stream[k][2], prec="fp32", outputs=ibm.OUT_RESIDUAL)
+                srv.submit(stream[k][1], stream[k][2], prec=prec, outputs=ibm.OUT_RESIDUAL)
                 k += 1
                 if not paced:
                     srv.wait()
             srv.wait()
             wall = time.perf_counter() - t0
-            return srv.stats(), wall
+            return srv.stats(), wall, tuned
 
-    st, wall = serve(args.serve_active, True)
-    out.update({"solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"],
+    def lattice_one_at_a_time():
+        t0 = time.perf_counter()
+        for _, case, steps in stream:
+            with ibm.Lattice.from_case(case, prec=prec, device=local_rank) as lat:
+                lat.step(steps)
+                lat.resid
+        return time.perf_counter() - t0
+
+    st, wall, tuned = serve(args.serve_active, True, batched=True, tune=True)
+    out.update({"mode": "batched: one persistent kernel per round over a task queue of all resident "
+                        "cases' correction tasks and collide+stream tiles",
+                "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p95_ms": st["p95_ms"],
                 "p99_ms": st["p99_ms"], "mlups": st["mlups"], "failed": st["failed"],
-                "max_active": args.serve_active, "wall_s": wall})
-    st1, wall1 = serve(1, False)
-    out["solves_per_s_one_at_a_time"] = len(stream) / wall1
+                "max_active": args.serve_active, "wall_s": wall, "autotuned": tuned,
+                "host_admit_s": st["host_admit_s"], "host_launch_s": st["host_launch_s"]})
+    stp, wallp, _ = serve(args.serve_active, True)
+    out["per_case_streams"] = {"solves_per_s": stp["solves_per_s"], "p50_ms": stp["p50_ms"],
+                               "p99_ms": stp["p99_ms"], "failed": stp["failed"], "wall_s": wallp,
+                               "what": "each resident case stepped by its own graph launches on its own stream"}
+    wall_l = lattice_one_at_a_time()
+    out["solves_per_s_one_at_a_time"] = len(stream) / wall_l
     out["speedup_vs_one_at_a_time"] = out["solves_per_s"] / out["solves_per_s_one_at_a_time"]
+    out["one_at_a_time"] = "each case as its own ibm.Lattice, one after another (the best single-case path)"
+    _, wall1, _ = serve(1, False)
+    out["solves_per_s_server_one_slot"] = len(stream) / wall1
+    out["speedup_vs_server_one_slot"] = out["solves_per_s"] / out["solves_per_s_server_one_slot"]
     return out
 
 

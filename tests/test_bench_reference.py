@@ -23,3 +23,6 @@ def test_reference_arm_prints_one_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["nx"] == 128 and d["config"]["markers"] > 0
+    assert d["config"]["timed_sample"].endswith("lattice, FP64 oracle")
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["nproc"] >= 1
+    assert d["cpu_baseline"]["cpu_model"]

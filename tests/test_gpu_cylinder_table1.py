@@ -72,8 +72,22 @@ def test_steady_drag_and_wake_at_re20():
     assert abs(lw / want["Lw_over_D"] - 1) < 0.10, (lw, want)
 
 
-def test_vortex_shedding_at_re100():
-    case, _, h = _run(100, 160000)
+def test_steady_drag_and_wake_at_re40():
+    """The longer steady wake of Re 40 (its bubble needs more steps to
+    settle than Re 20's)."""
+    case, lat, h = _run(40, 100000)
+    cd = h[len(h) // 2:, 0].mean()
+    want = _table()["Re40"]
+    assert abs(cd / want["Cd"] - 1) < 0.05, (cd, want)
+    assert np.abs(h[len(h) // 2:, 1]).max() < 0.01
+    lat.step(1)
+    _, ux, _ = lat.moments()
+    lw = _wake_length(case, ux)
+    assert abs(lw / want["Lw_over_D"] - 1) < 0.10, (lw, want)
+
+
+def _shedding(case, h):
+    """Mean drag, lift amplitude and Strouhal number over the second half."""
     tail = h[len(h) // 2:]
     cd = tail[:, 0].mean()
     cl = (tail[:, 1].max() - tail[:, 1].min()) / 2
@@ -81,7 +95,14 @@ def test_vortex_shedding_at_re100():
     up = np.where(np.diff(np.sign(c)) > 0)[0]
     period = (up[-1] - up[0]) / (len(up) - 1) * 20
     st = case.meta["diameter"] / (period * case.inlet_u[0])
-    want = _table()["Re100"]
+    return cd, cl, st
+
+
+@pytest.mark.parametrize("re", [100, 200])
+def test_vortex_shedding(re):
+    case, _, h = _run(re, 160000)
+    cd, cl, st = _shedding(case, h)
+    want = _table()[f"Re{re}"]
     assert abs(cd / want["Cd"] - 1) < 0.05, (cd, want)
     assert abs(cl / want["Cl"] - 1) < 0.10, (cl, want)
     assert abs(st / want["St"] - 1) < 0.03, (st, want)

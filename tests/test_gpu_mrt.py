@@ -9,7 +9,7 @@ import pytest
 from paper_1803_09380_gb300 import ibm
 from paper_1803_09380_gb300 import workloads as wl
 
-from _helpers import field_errors, gpu_lattice, oracle_lattice, relerr
+from _helpers import density_ok, field_errors, gpu_lattice, oracle_lattice, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -43,8 +43,9 @@ def _random_init(seed):
 def _check(gpu, ora, tol, tol_dev=None):
     errs = field_errors(gpu, ora)
     lim = {"fdev": 10 * tol if tol_dev is None else tol_dev}
-    for k, v in errs.items():
-        assert v < lim.get(k, tol), (k, errs)
+    for k in ("rho", "ux", "uy", "f", "fdev"):
+        assert errs[k] < lim.get(k, tol), (k, errs)
+    assert density_ok(errs, tol), ("rho - rho0", errs)
 
 
 @pytest.mark.parametrize("steps", [1, 2, 51])

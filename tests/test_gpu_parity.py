@@ -15,7 +15,7 @@ import oracle
 from paper_1803_09380_gb300 import ibm
 from paper_1803_09380_gb300 import workloads as wl
 
-from _helpers import field_errors, gpu_lattice, oracle_lattice, relerr
+from _helpers import density_ok, field_errors, gpu_lattice, oracle_lattice, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -37,9 +37,10 @@ def _assert_fields(gpu, ora, tol, rho0=1.0, tol_dev=None):
     oracle's rounding floor on the deviations, see field_errors)."""
     errs = field_errors(gpu, ora, rho0)
     lim = {"fdev": 10 * tol if tol_dev is None else tol_dev}
-    for k, v in errs.items():
+    for k in ("rho", "ux", "uy", "f", "fdev"):
         t = lim.get(k, tol)
-        assert v < t, f"{k}: normwise error {v:.3e} >= {t:.1e} ({errs})"
+        assert errs[k] < t, f"{k}: normwise error {errs[k]:.3e} >= {t:.1e} ({errs})"
+    assert density_ok(errs, tol, rho0), f"rho - rho0: {errs}"
 
 
 def _random_init(seed):
@@ -191,6 +192,25 @@ def test_settling_pair_fp64():
     assert relerr(gpu.markers, ora.markers) < 1e-14
 
 
+def test_settling_pair_fp64_100_steps_at_the_fp64_bound():
+    """The same two disks after 100 steps, held to the FP64 bound of 1e-12
+    on velocity, body velocities and force (measured 8.7e-13, 4.6e-13 and
+    7.9e-13 on GB300).  The deviations f - w_i, whose scale here is only
+    ~1e-4, reach 1.45e-12: the lagged internal-mass terms of Eqs. 37-38 feed
+    the force difference of each step back into the body velocity with gain
+    rho_f / (rho_s - rho_f) = 5, so 3e-12 is their floor."""
+    case = wl.settling_pair(nx=64, ny=130, diameter=10.0, density_ratio=1.2, gravity=2e-4)
+    ora, gpu = _run_pair(case, 100)
+    errs = field_errors(gpu, ora)
+    assert max(errs["rho"], errs["f"], errs["ux"], errs["uy"]) < TOL64, errs
+    assert errs["fdev"] < 3e-12 and density_ok(errs, TOL64), errs
+    bg, bo = gpu.bodies, ora.bodies
+    assert np.max(np.abs(bg[:, 0:2] - bo[:, 0:2])) < 1e-12
+    assert relerr(bg[:, 2:4], bo[:, 2:4]) < TOL64
+    assert relerr(bg[:, 6:9], bo[:, 6:9]) < TOL64
+    assert relerr(gpu.markers, ora.markers) < 1e-14
+
+
 def test_prescribed_motion_fp64():
     xy, ds = wl.ring(30.2, 31.7, 6.0)
     body = wl.Body(xy, ds, wl.BODY_PRESCRIBED, xc=(30.2, 31.7), u=(0.01, -0.004), omega=0.002,
@@ -202,9 +222,10 @@ def test_prescribed_motion_fp64():
 
 
 # ------------------------------------------------------------------ FP32
-def test_couette_64_fp32_steady_velocity():
-    """FP32 storage and arithmetic: steady velocity within 1e-4 of the FP64
-    oracle (3000 steps, residual drift of the transient below 1e-6)."""
+def test_couette_64_fp32_velocity_3000_steps():
+    """FP32 storage and arithmetic: velocity within 1e-4 of the FP64 oracle
+    after 3000 steps of the spin-up (not yet steady; the steady field is
+    checked element by element in test_gpu_steady.py)."""
     case = wl.couette_64()
     ora, gpu = _run_pair(case, 3000, prec="fp32")
     _, ox, oy = ora.moments()
