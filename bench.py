@@ -62,6 +62,9 @@ def parse():
                    help="keep the library's default correction grid instead of timing candidates")
     p.add_argument("--ib-threads", type=int, default=0,
                    help="threads per correction-kernel CTA (0: the library's choice)")
+    p.add_argument("--ib-phases", type=int, choices=[-1, 0, 1, 2], default=-1,
+                   help="correction loop as one persistent kernel (0), phase kernels (1), or "
+                        "persistent kernels around a Jacobi cluster (2); -1: the library's default")
     p.add_argument("--serve-requests", type=int, default=512)
     p.add_argument("--serve-steps", type=int, default=500)
     p.add_argument("--serve-prec", choices=list(BYTES_PER_POP), default="fp32")
@@ -345,13 +348,15 @@ def run_ours(args, rank, world, local_rank, dist):
     N2 = case.nx * case.ny
     lat = ibm.Lattice.from_case(case, prec=args.prec, device=local_rank)
     tuned = None
+    if args.ib_phases >= 0:
+        ibm.ibm_set_option(lat.h, ibm.IBM_OPT_IB_PHASES, args.ib_phases)
     if args.ib_ctas:
         lat.set_ib_ctas(args.ib_ctas)
     elif not args.no_autotune:
         # the library's measured choice of the correction grid (its runs are
         # real steps and count as warm-up)
         sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-        tuned = lat.autotune_ib([sms * k // 8 for k in (4, 5, 6, 7, 8)], steps_each=50)
+        tuned = lat.autotune_ib([sms * k // 8 for k in (2, 3, 4, 5, 6, 7, 8)], steps_each=50)
     if args.ib_threads:
         lat.set_ib_threads(args.ib_threads)
     stream = lat._stream

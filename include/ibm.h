@@ -244,7 +244,8 @@ enum {
                            markers, 3 per 4 SMs above that; n > 0 = min(n, SMs).  2..16 CTAs
                            run as one thread-block cluster when the device can schedule it.
                            Results do not depend on it. */
-  IBM_OPT_IB_THREADS = 2, /* threads per correction-kernel CTA: 256 (default), 512 or 1024 */
+  IBM_OPT_IB_THREADS = 2, /* threads per correction-kernel CTA: 256 (default), 512 or 1024
+                           (with IBM_OPT_IB_PHASES = 2: per CTA of the Jacobi cluster) */
   IBM_OPT_WATCHDOG_STEPS = 3, /* K > 0: after every K steps (at the next 8-step block boundary)
                            scan every stored population for NaN/Inf; a hit makes the next
                            synchronising call return IBM_ERR_DIVERGED.  0 (default): no scan.
@@ -253,6 +254,17 @@ enum {
   IBM_OPT_BARRIER_LIMIT_US = 4, /* wait limit of the correction kernel's global-memory grid
                            barrier in microseconds, [100, 6e7] (default 2 s); a wait that runs
                            out makes the next synchronising call return IBM_ERR_TIMEOUT */
+  IBM_OPT_IB_PHASES = 6,     /* how the correction loop of section 2.3 is launched.  0 (default):
+                           one persistent kernel with a grid barrier between phases.  1: a chain
+                           of short kernels, one per phase (band gather, interpolation, each
+                           Jacobi iteration, final residual and history, second moments),
+                           ordered by the stream; their CTAs leave the SMs as soon as their
+                           share is done.  2: gather and interpolation in one persistent kernel,
+                           the Jacobi iterations in one thread-block cluster (up to 16 CTAs)
+                           holding A^n in distributed shared memory, history and moments in a
+                           second persistent kernel; boundaries of at most 512 markers, or a
+                           device that cannot schedule the cluster, keep mode 0.  Results do
+                           not depend on it (bit for bit). */
   IBM_OPT_TEST_DROP_ARRIVAL = 5 /* testing the timeout path only: 1 makes the last CTA of the
                            correction kernel skip its arrival at the first grid barrier of each
                            step, so the other CTAs' waits run out (bounded by

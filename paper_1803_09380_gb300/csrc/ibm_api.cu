@@ -189,6 +189,16 @@ ibm_status fold_events(Ctx* h) {
   return IBM_OK;
 }
 
+// Band nodes of the current band (sizes the grids of the phase kernels;
+// synchronises the stream).
+ibm_status count_band(Ctx* h) {
+  int ctr[CTR_COUNT] = {0, 0, 0, 0};
+  IBM_CK(h, cudaMemcpyAsync(ctr, h->dctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
+  IBM_CK(h, cudaStreamSynchronize(h->stream));
+  h->nband_host = std::min(ctr[CTR_NBAND], h->bcap);
+  return IBM_OK;
+}
+
 // The NaN/Inf scan of the whole lattice after every watchdog_steps steps
 // (checked between graph replays, so with blocks of steps it runs at the
 // first block boundary at or after the due step).
@@ -225,6 +235,8 @@ void choose_ib_grid(Ctx& c) {
     if (c.ib_cluster_max < 0) c.ib_cluster_max = ib_max_cluster(c.prec, c.ib_threads);
     c.ib_cluster = c.ib_grid <= c.ib_cluster_max;
   }
+  // the Jacobi cluster of IBM_OPT_IB_PHASES = 2 (none: the persistent kernel)
+  c.ib_jc_cluster = c.ib_phases == 2 && M > kSmallIbMarkers ? jacobi_cluster_size(c.prec, M, c.ib_threads) : 0;
 }
 
 ibm_status upload_markers(Ctx* h) {
@@ -654,6 +666,10 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags) {
     if (c.nm > 0 && !c.band_valid) {
       launch_band_build(c, c.stream);
       c.band_valid = true;
+      if (c.ib_phases == 1) {
+        ibm_status st = count_band(h);
+        if (st != IBM_OK) return st;
+      }
     }
     const bool want_macro = !(flags & IBM_STEP_NO_MACRO);
     for (int k = 0; k < nsteps;) {
@@ -983,6 +999,16 @@ ibm_status ibm_set_option(ibm_handle h, int option, long long value) {
     h->ib_cluster_max = -1;
     choose_ib_grid(*h);
     destroy_graphs(*h);
+    return IBM_OK;
+  }
+  if (option == IBM_OPT_IB_PHASES) {
+    if (value < 0 || value > 2) return fail(h, IBM_ERR_INVALID, "IBM_OPT_IB_PHASES must be 0, 1 or 2");
+    DeviceGuard guard(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->ib_phases = (int)value;
+    choose_ib_grid(*h);
+    destroy_graphs(*h);
+    if (h->ib_phases == 1 && h->band_valid) return count_band(h);
     return IBM_OK;
   }
   if (option == IBM_OPT_WATCHDOG_STEPS) {

@@ -2,6 +2,8 @@
 // step (the correction loop, the band build, the band collide+stream, the
 // body update) and their launchers.  The device code they run is in
 // ibm_ib.cuh.
+#include <algorithm>
+
 #include "ibm_ib.cuh"
 
 namespace ibm {
@@ -70,6 +72,221 @@ template <int P, int PAR, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) k_ib_step(IbArgs<P> a) {
   ib_step_body<P, PAR, NT>(a, blockIdx.x, gridDim.x);
 }
+
+// The correction loop as a chain of short kernels on the high-priority
+// stream (IBM_OPT_IB_PHASES): the CTAs of each phase leave their SMs as soon
+// as their share is done, instead of holding registers at grid barriers
+// while the band-free collide+stream needs the SMs; kernel boundaries order
+// the phases.  Each phase folds its CTA's residual maximum into the history
+// with an integer maximum of the bit pattern (order-independent).
+template <int P, int PAR>
+__global__ void __launch_bounds__(kIbThreads) k_ib_gather(IbArgs<P> a) {
+  typedef typename Prec<P>::R R;
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k <= a.N; k += kIbThreads) a.resid[k] = R(0);
+  ib_phase_gather<P, PAR, kIbThreads>(a, blockIdx.x * kIbThreads + threadIdx.x, gridDim.x * kIbThreads,
+                                      min(a.ctr[CTR_NBAND], a.bcap));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kIbThreads) k_ib_interp(IbArgs<P> a) {
+  __shared__ typename Prec<P>::R red[kIbThreads / 32];
+  ib_phase_interp<P, kIbThreads>(a, blockIdx.x * kIbThreads + threadIdx.x, gridDim.x * kIbThreads, red);
+  fold_max<P, kIbThreads>(red, a.resid);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kIbThreads) k_ib_jacobi(IbArgs<P> a, int n) {
+  __shared__ typename Prec<P>::R red[kIbThreads / 32];
+  ib_phase_jacobi<P, kIbThreads>(a, n, blockIdx.x * kIbThreads + threadIdx.x, gridDim.x * kIbThreads, red);
+  fold_max<P, kIbThreads>(red, a.resid + n);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kIbThreads) k_ib_final(IbArgs<P> a) {
+  __shared__ typename Prec<P>::R red[kIbThreads / 32];
+  __shared__ double sh[96];
+  const int tid = blockIdx.x * kIbThreads + threadIdx.x, nth = gridDim.x * kIbThreads;
+  ib_phase_final<P, kIbThreads>(a, tid, nth, nth - 1 - tid, min(a.ctr[CTR_NBAND], a.bcap), blockIdx.x,
+                                gridDim.x, red, sh);
+  fold_max<P, kIbThreads>(red, a.resid + a.N);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kIbThreads) k_ib_moments(IbArgs<P> a) {
+  __shared__ double sh[96];
+  if (blockIdx.x == 0 && threadIdx.x == 0) ib_check_resid<P>(a);
+  ib_phase_moments<P, kIbThreads>(a, blockIdx.x * kIbThreads + threadIdx.x, gridDim.x * kIbThreads,
+                                  blockIdx.x, gridDim.x, sh);
+}
+
+// The correction loop with its Jacobi iterations in one thread-block
+// cluster (IBM_OPT_IB_PHASES = 2): a persistent kernel gathers the band and
+// interpolates (one grid barrier); the cluster iterates with the markers'
+// momentum deviations A^n in shared memory -- each CTA holds a contiguous
+// slice of the markers, reads its neighbours' values from the other CTAs'
+// shared memory and meets them at the hardware cluster barrier -- and
+// writes every level A^n to the history; a second persistent kernel does the
+// history pass, the forces and the second moments (one grid barrier).
+template <int P, int PAR, int NT>
+__global__ void __launch_bounds__(NT, 3) k_ib_pre(IbArgs<P> a) {
+  typedef typename Prec<P>::R R;
+  __shared__ R red[NT / 32];
+  const int tid = blockIdx.x * NT + threadIdx.x, nth = gridDim.x * NT;
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k <= a.N; k += NT) a.resid[k] = R(0);
+  ib_phase_gather<P, PAR, NT>(a, tid, nth, min(a.ctr[CTR_NBAND], a.bcap));
+  grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster, a.bar_limit_ns, gridDim.x);
+  ib_phase_interp<P, NT>(a, tid, nth, red);
+  fold_max<P, NT>(red, a.resid);
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 3) k_ib_post(IbArgs<P> a) {
+  typedef typename Prec<P>::R R;
+  __shared__ R red[NT / 32];
+  __shared__ double sh[96];
+  const int tid = blockIdx.x * NT + threadIdx.x, nth = gridDim.x * NT;
+  ib_phase_final<P, NT>(a, tid, nth, nth - 1 - tid, min(a.ctr[CTR_NBAND], a.bcap), blockIdx.x, gridDim.x,
+                        red, sh);
+  grid_barrier<R>(a.bar, a.ctr, red, a.resid + a.N, a.cluster, a.bar_limit_ns, gridDim.x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ib_check_resid<P>(a);
+  ib_phase_moments<P, NT>(a, tid, nth, blockIdx.x, gridDim.x, sh);
+}
+
+__device__ __forceinline__ unsigned int cluster_rank() {
+  unsigned int r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Shared-memory address `addr` of this CTA mapped to cluster CTA `rank`.
+__device__ __forceinline__ unsigned int dsmem_map(unsigned int addr, unsigned int rank) {
+  unsigned int r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void dsmem_ld(unsigned int addr, float2& v) {
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+}
+__device__ __forceinline__ void dsmem_ld(unsigned int addr, double2& v) {
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
+}
+
+// Shared memory of one CTA of the Jacobi cluster for a slice of `per`
+// markers: A^n and A^{n+1} and b (pairs), the first kRowHead entries of each
+// G row as weights and cluster addresses of the coupled markers' A slots,
+// the row lengths and the interpolated densities.
+template <class R>
+__host__ __device__ constexpr size_t jacobi_smem_bytes(int per) {
+  return (size_t)per * (3 * 2 * sizeof(R) + (kRowHead + 1) * sizeof(R) + kRowHead * sizeof(unsigned int) +
+                        sizeof(int));
+}
+
+// Jacobi iterations n = 1 .. N-1 (A^{n+1} = A^n + b - G A^n) by the
+// `per`-marker slices of the cluster's CTAs (the residual of A^N is the
+// history pass's).  The G rows are constant through the iterations: their
+// first kRowHead entries are staged once as weights and peer addresses, so
+// an iteration is kRowHead independent distributed-shared-memory loads per
+// marker, summed in the row's stored (ascending marker) order as
+// deviation() sums them, then one hardware cluster barrier.
+template <int P, int NTC>
+__global__ void __launch_bounds__(NTC, 1024 / NTC) k_ib_jacobi_cluster(IbArgs<P> a, int per) {
+  typedef typename Prec<P>::R R;
+  typedef typename Vec2<R>::T V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* As = reinterpret_cast<V*>(smem_raw);                    // [2][per]: A^n and A^{n+1} of the slice
+  V* bs = As + 2 * per;                                      // [per]: b
+  R* wt = reinterpret_cast<R*>(bs + per);                    // [kRowHead][per]
+  R* rs = wt + kRowHead * per;                               // [per]: interpolated density
+  unsigned int* ad = reinterpret_cast<unsigned int*>(rs + per);   // [kRowHead][per]
+  int* nc = reinterpret_cast<int*>(ad + kRowHead * per);     // [per]: row length
+  __shared__ R red[2 * (NTC / 32)];
+  const unsigned int crank = cluster_rank();
+  const int M = a.M, N = a.N;
+  const int m0 = (int)crank * per, cnt = max(0, min(M, m0 + per) - m0);
+  V* Ah = reinterpret_cast<V*>(a.Ah);
+  const unsigned int base = (unsigned int)__cvta_generic_to_shared(As);
+  for (int i = threadIdx.x; i < cnt; i += NTC) {
+    const int l = m0 + i;
+    As[i] = Ah[M + l];                                       // A^1 = b
+    V b;
+    b.x = a.mq[4 * l + 1];
+    b.y = a.mq[4 * l + 2];
+    bs[i] = b;
+    rs[i] = a.mq[4 * l];
+    const int k1 = a.gcnt[l];
+    nc[i] = k1;
+    const Ent<R>* row = a.G + (long long)l * kGCap;
+#pragma unroll
+    for (int j = 0; j < kRowHead; ++j) {
+      unsigned int addr = base + (unsigned int)(i * sizeof(V));
+      R w = R(0);
+      if (j < k1) {
+        const Ent<R> q = row[j];
+        const int owner = q.m / per;
+        addr = dsmem_map(base + (unsigned int)((q.m - owner * per) * sizeof(V)), (unsigned int)owner);
+        w = q.w;
+      }
+      ad[j * per + i] = addr;
+      wt[j * per + i] = w;
+    }
+  }
+  cluster_sync_all();
+  const unsigned int half = (unsigned int)(per * sizeof(V));
+  int cur = 0;
+  for (int n = 1; n < N; ++n) {
+    const V* Acur = As + cur * per;
+    V* Anxt = As + (cur ^ 1) * per;
+    const unsigned int off = cur ? half : 0u;
+    R rmax = R(0);
+    for (int i = threadIdx.x; i < cnt; i += NTC) {
+      const int l = m0 + i, k1 = nc[i];
+      V v[kRowHead];
+#pragma unroll
+      for (int j = 0; j < kRowHead; ++j)
+        if (j < k1) dsmem_ld(ad[j * per + i] + off, v[j]);
+      R sx = R(0), sy = R(0);
+#pragma unroll
+      for (int j = 0; j < kRowHead; ++j)
+        if (j < k1) {
+          const R w = wt[j * per + i];
+          sx += w * v[j].x;
+          sy += w * v[j].y;
+        }
+      for (int k = kRowHead; k < k1; ++k) {                  // rare long rows: the rest from G
+        const Ent<R> q = a.G[(long long)l * kGCap + k];
+        const int owner = q.m / per;
+        V u;
+        dsmem_ld(dsmem_map(base + off + (unsigned int)((q.m - owner * per) * sizeof(V)), (unsigned int)owner), u);
+        sx += q.w * u.x;
+        sy += q.w * u.y;
+      }
+      const V b = bs[i];
+      const R djx = b.x - sx, djy = b.y - sy;
+      V an;
+      an.x = Acur[i].x + djx;
+      an.y = Acur[i].y + djy;
+      Anxt[i] = an;
+      Ah[(long long)(n + 1) * M + l] = an;
+      rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / rs[i]));
+    }
+    R* rd = red + (n & 1) * (NTC / 32);                      // two buffers: no block barrier
+    warp_max_to<R>(rmax, rd);
+    cluster_sync_all();                                       // every read of A^n is done
+    if (threadIdx.x == 0) {
+      R m = rd[0];
+      for (int k = 1; k < NTC / 32; ++k) m = nanmax(m, rd[k]);
+      if (m > R(0) || m != m) AtomicBits<R>::max(a.resid + n, m);
+    }
+    cur ^= 1;
+  }
+}
+
+constexpr int kJacobiSmemMax = 192 * 1024;                  // dynamic shared memory of one slice pair
 
 // Collide+stream of the 32-node row segments that hold band nodes, after
 // the correction kernel has corrected them: one warp per segment.
@@ -164,10 +381,64 @@ static void launch_band_collide(dim3 g2, dim3 b2, cudaStream_t s, int prio, cons
   }
 }
 
+// One cluster of h.ib_jc_cluster CTAs of NTC threads runs the Jacobi
+// iterations (IBM_OPT_IB_PHASES = 2).
+template <int P, int NTC>
+static void launch_jacobi_cluster(const Ctx& h, cudaStream_t s, const IbArgs<P>& a) {
+  const int C = h.ib_jc_cluster, per = (h.nm + C - 1) / C;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(NTC);
+  cfg.dynamicSmemBytes = jacobi_smem_bytes<typename Prec<P>::R>(per);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = h.ib_prio;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = C;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaLaunchKernelEx(&cfg, k_ib_jacobi_cluster<P, NTC>, a, per);
+}
+
 template <int P>
 static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
   if (h.nm == 0) return;
   IbArgs<P> a = make_ib_args<P>(h);
+  if (h.ib_phases == 2 && h.ib_jc_cluster >= 2) {
+    // gather + interpolation | Jacobi in one cluster | history, forces, moments
+    a.apply = 0;
+    const dim3 grid(h.ib_grid), block(kIbThreads);
+    auto go = [&](auto kern) {
+      if (a.cluster) launch_prio_cluster(kern, grid, block, s, h.ib_prio, a);
+      else launch_prio(kern, grid, block, s, h.ib_prio, a);
+    };
+    if (parity == 0) go(k_ib_pre<P, 0, kIbThreads>);
+    else go(k_ib_pre<P, 1, kIbThreads>);
+    if (h.desc.n_corr > 1) {
+      switch (h.ib_threads) {
+        case 1024: launch_jacobi_cluster<P, 1024>(h, s, a); break;
+        case 512: launch_jacobi_cluster<P, 512>(h, s, a); break;
+        default: launch_jacobi_cluster<P, 256>(h, s, a);
+      }
+    }
+    go(k_ib_post<P, kIbThreads>);
+  } else if (h.ib_phases == 1) {
+    // one kernel per phase; grids sized by the work (every loop strides, so
+    // any size is correct): markers, and band nodes as last counted
+    auto ctas = [](long long items) { return dim3((unsigned)std::max(1LL, (items + kIbThreads - 1) / kIbThreads)); };
+    const long long band = std::max<long long>(h.nband_host + h.nband_host / 4, 1);
+    const dim3 gm = ctas(h.nm), gb = ctas(band), gf = ctas(std::max<long long>(h.nm, band)), bt(kIbThreads);
+    a.apply = 0;
+    if (parity == 0) launch_prio(k_ib_gather<P, 0>, gb, bt, s, h.ib_prio, a);
+    else launch_prio(k_ib_gather<P, 1>, gb, bt, s, h.ib_prio, a);
+    launch_prio(k_ib_interp<P>, gm, bt, s, h.ib_prio, a);
+    for (int n = 1; n < h.desc.n_corr; ++n) launch_prio(k_ib_jacobi<P>, gm, bt, s, h.ib_prio, a, n);
+    launch_prio(k_ib_final<P>, gf, bt, s, h.ib_prio, a);
+    launch_prio(k_ib_moments<P>, gm, bt, s, h.ib_prio, a);
+  } else {
   const dim3 grid(h.ib_grid), block(h.ib_threads);
   switch (h.ib_threads) {
     case 512:
@@ -178,6 +449,7 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
       break;
     default:
       launch_ib<P, kIbThreads>(parity, a.cluster != 0, grid, block, s, h.ib_prio, a);
+  }
   }
   // the band segments, once corrected
   if (h.band_collide) {
@@ -295,6 +567,68 @@ void launch_body_update(const Ctx& h, cudaStream_t s) {
   if (h.nb == 0 || !h.any_moving) return;
   if (h.r_bytes == 8) body_update_t<double>(h, s);
   else body_update_t<float>(h, s);
+}
+
+
+// Largest cluster (at most 16 CTAs of NTC threads) that can run the Jacobi
+// iterations of M markers with the slices in shared memory; 0 when none can.
+template <int P, int NTC>
+static int jacobi_cluster_t(int M) {
+  void (*kern)(IbArgs<P>, int) = k_ib_jacobi_cluster<P, NTC>;
+  // the attributes allow any slice size up to kJacobiSmemMax, so that
+  // lattices with different marker counts can share the kernel
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacobiSmemMax) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  for (int c = kMaxIbCluster; c >= 2; --c) {
+    const int per = (M + c - 1) / c;
+    const size_t smem = jacobi_smem_bytes<typename Prec<P>::R>(per);
+    if (smem > (size_t)kJacobiSmemMax) break;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(NTC);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (n > 0) return c;
+  }
+  return 0;
+}
+
+template <int P>
+static int jacobi_cluster_p(int M, int threads) {
+  switch (threads) {
+    case 1024: return jacobi_cluster_t<P, 1024>(M);
+    case 512: return jacobi_cluster_t<P, 512>(M);
+    default: return jacobi_cluster_t<P, 256>(M);
+  }
+}
+
+int jacobi_cluster_size(int prec, int M, int threads) {
+  int dev = 0, ok = 0;
+  if (M < 2 || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, dev) != cudaSuccess || !ok) {
+    cudaGetLastError();
+    return 0;
+  }
+  switch (prec) {
+    case PREC_FP64: return jacobi_cluster_p<PREC_FP64>(M, threads);
+    case PREC_FP32: return jacobi_cluster_p<PREC_FP32>(M, threads);
+    case PREC_FP16_DEV: return jacobi_cluster_p<PREC_FP16_DEV>(M, threads);
+    default: return jacobi_cluster_p<PREC_BF16_DEV>(M, threads);
+  }
 }
 
 }  // namespace ibm

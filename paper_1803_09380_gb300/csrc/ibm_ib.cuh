@@ -540,24 +540,16 @@ __device__ __forceinline__ void deviation(const Args& a, int l, const R* __restr
   djx = a.mq[4 * l + 1] - sx;
   djy = a.mq[4 * l + 2] - sy;
 }
-// The whole correction loop of one step, run by CTA `rank` of the nranks
-// CTAs (NT threads each) that share it.
+// The correction loop of one step in phases.  Each phase runs on nth
+// threads numbered tid (band-node work from the other end, rtid = nth - 1 -
+// tid), grouped in CTAs of NT threads numbered rank of nranks; a phase reads
+// only what earlier phases wrote.  ib_step_body separates them with grid
+// barriers inside one persistent kernel; the phase kernels of ibm_ib.cu
+// separate them with kernel boundaries.  Phases that contribute to the
+// residual history leave their warps' maxima in red[].
 template <int P, int PAR, int NT>
-__device__ void ib_step_body(const IbArgs<P>& a, int rank, int nranks) {
+__device__ __forceinline__ void ib_phase_gather(const IbArgs<P>& a, int tid, int nth, int nband) {
   typedef typename Prec<P>::R R;
-  __shared__ R red[NT / 32];
-  __shared__ double sh[96];
-  const int tid = rank * NT + threadIdx.x;
-  const int nth = nranks * NT;
-  const int rtid = nth - 1 - tid;                  // band work starts from the other end
-  const int nband = min(a.ctr[CTR_NBAND], a.bcap);
-  const int M = a.M, N = a.N;
-
-  // residual history of this step starts at zero (first read-modify-write
-  // after the next barrier)
-  if (rank == 0)
-    for (int k = threadIdx.x; k <= N; k += NT) a.resid[k] = R(0);
-
   // gather rho and j^0 at every band node
   for (int b = tid; b < nband; b += nth) {
     const int n = a.bnode[b];
@@ -581,9 +573,13 @@ __device__ void ib_step_body(const IbArgs<P>& a, int rank, int nranks) {
     a.bq[8 * b + 1] = jx;
     a.bq[8 * b + 2] = jy;
   }
-  grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster, a.bar_limit_ns, nranks,
-                  a.drop_arrival && rank == nranks - 1);
+}
 
+template <int P, int NT>
+__device__ __forceinline__ void ib_phase_interp(const IbArgs<P>& a, int tid, int nth,
+                                                typename Prec<P>::R* red) {
+  typedef typename Prec<P>::R R;
+  const int M = a.M, N = a.N;
   // phase 0: interpolate rho*, J*^0 (Eq. 22b with Eq. 28 in moment form),
   // b_l = rho* U_l - J*^0 and A^1 = b (A^0 = 0); band nodes: S2 = j^0 j^0
   {
@@ -618,25 +614,32 @@ __device__ void ib_step_body(const IbArgs<P>& a, int rank, int nranks) {
     }
     warp_max_to<R>(rmax, red);
   }
-  grid_barrier<R>(a.bar, a.ctr, red, a.resid, a.cluster, a.bar_limit_ns, nranks);
+}
 
-  // phases 1..N-1: Jacobi iteration A^{n+1} = A^n + b - G A^n; band nodes
-  // add j^n j^n to S2
-  for (int n = 1; n < N; ++n) {
-    const R* An = a.Ah + (long long)n * 2 * M;
-    R* An1 = a.Ah + (long long)(n + 1) * 2 * M;
-    R rmax = R(0);
-    for (int l = tid; l < M; l += nth) {
-      R djx, djy;
-      deviation<R>(a, l, An, djx, djy);
-      An1[2 * l] = An[2 * l] + djx;
-      An1[2 * l + 1] = An[2 * l + 1] + djy;
-      rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
-    }
-    warp_max_to<R>(rmax, red);
-    grid_barrier<R>(a.bar, a.ctr, red, a.resid + n, a.cluster, a.bar_limit_ns, nranks);
+// Jacobi iteration n (1 <= n < N): A^{n+1} = A^n + b - G A^n.
+template <int P, int NT>
+__device__ __forceinline__ void ib_phase_jacobi(const IbArgs<P>& a, int n, int tid, int nth,
+                                                typename Prec<P>::R* red) {
+  typedef typename Prec<P>::R R;
+  const int M = a.M;
+  const R* An = a.Ah + (long long)n * 2 * M;
+  R* An1 = a.Ah + (long long)(n + 1) * 2 * M;
+  R rmax = R(0);
+  for (int l = tid; l < M; l += nth) {
+    R djx, djy;
+    deviation<R>(a, l, An, djx, djy);
+    An1[2 * l] = An[2 * l] + djx;
+    An1[2 * l + 1] = An[2 * l + 1] + djy;
+    rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / a.mq[4 * l]));
   }
+  warp_max_to<R>(rmax, red);
+}
 
+template <int P, int NT>
+__device__ __forceinline__ void ib_phase_final(const IbArgs<P>& a, int tid, int nth, int rtid, int nband, int rank,
+                                               int nranks, typename Prec<P>::R* red, double* sh) {
+  typedef typename Prec<P>::R R;
+  const int M = a.M, N = a.N;
   // final phase: residual r^N; per band node the final spread D^N and
   // sum_n j^n j^n over the iterations (entries gathered once, then every
   // A^n read eight at a time)
@@ -736,15 +739,23 @@ __device__ void ib_step_body(const IbArgs<P>& a, int rank, int nranks) {
       }
     }
   }
-  grid_barrier<R>(a.bar, a.ctr, red, a.resid + N, a.cluster, a.bar_limit_ns, nranks);
-  // r^N is complete: a non-finite residual means the state has diverged; one
-  // above corr_tol is reported as a warning
-  if (rank == 0 && threadIdx.x == 0) {
-    const R rN = a.resid[N];
-    if (!isfinite(rN)) atomicOr(&a.ctr[CTR_ERR], ERR_DIVERGED);
-    else if (a.corr_tol > R(0) && rN > a.corr_tol) atomicOr(&a.ctr[CTR_ERR], WARN_NOT_CONV);
-  }
+}
 
+// r^N is complete: a non-finite residual means the state has diverged; one
+// above corr_tol is reported as a warning (one thread).
+template <int P>
+__device__ __forceinline__ void ib_check_resid(const IbArgs<P>& a) {
+  typedef typename Prec<P>::R R;
+  const R rN = a.resid[a.N];
+  if (!isfinite(rN)) atomicOr(&a.ctr[CTR_ERR], ERR_DIVERGED);
+  else if (a.corr_tol > R(0) && rN > a.corr_tol) atomicOr(&a.ctr[CTR_ERR], WARN_NOT_CONV);
+}
+
+template <int P, int NT>
+__device__ __forceinline__ void ib_phase_moments(const IbArgs<P>& a, int tid, int nth, int rank, int nranks,
+                                                 double* sh) {
+  typedef typename Prec<P>::R R;
+  const int M = a.M, N = a.N;
   // second-moment deviations summed over the iterations:
   // C_l = N rho* U U - sum_x W_l(x) / rho(x) sum_n j^n j^n
   if (N > 0) {
@@ -789,18 +800,64 @@ __device__ void ib_step_body(const IbArgs<P>& a, int rank, int nranks) {
     }
   }
 
-  if (a.apply) grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster, a.bar_limit_ns, nranks);     // the apply reads every C_l
+}
 
-  // Eq. 27 summed over the iterations, unless k_band_collide applies it
-  // just before it streams the band segments
-  if (N > 0 && a.apply) {
-    for (int b = tid; b < nband; b += nth) {
-      const int n = a.bnode[b];
-      apply_band_correction<P>(a.g, a.c, a.A, PAR, a.bq, a.bcnt, a.ent, a.Cm, b, n % a.g.nx, n / a.g.nx);
-    }
+// Folds the CTA's warp maxima in red[] into *dst (integer maximum of the
+// bit pattern: order-independent).
+template <int P, int NT>
+__device__ __forceinline__ void fold_max(const typename Prec<P>::R* red, typename Prec<P>::R* dst) {
+  typedef typename Prec<P>::R R;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R m = red[0];
+    for (int k = 1; k < NT / 32; ++k) m = nanmax(m, red[k]);
+    if (m > R(0) || m != m) AtomicBits<R>::max(dst, m);
   }
+}
 
+// Eq. 27 summed over the iterations at every band node (when the correction
+// kernel applies it itself).
+template <int P, int PAR>
+__device__ __forceinline__ void ib_phase_apply(const IbArgs<P>& a, int tid, int nth, int nband) {
+  for (int b = tid; b < nband; b += nth) {
+    const int n = a.bnode[b];
+    apply_band_correction<P>(a.g, a.c, a.A, PAR, a.bq, a.bcnt, a.ent, a.Cm, b, n % a.g.nx, n / a.g.nx);
+  }
+}
 
+// The whole correction loop of one step, run by CTA `rank` of the nranks
+// CTAs (NT threads each) that share it.
+template <int P, int PAR, int NT>
+__device__ void ib_step_body(const IbArgs<P>& a, int rank, int nranks) {
+  typedef typename Prec<P>::R R;
+  __shared__ R red[NT / 32];
+  __shared__ double sh[96];
+  const int tid = rank * NT + threadIdx.x;
+  const int nth = nranks * NT;
+  const int rtid = nth - 1 - tid;                  // band work starts from the other end
+  const int nband = min(a.ctr[CTR_NBAND], a.bcap);
+  const int N = a.N;
+  // residual history of this step starts at zero (first read-modify-write
+  // after the next barrier)
+  if (rank == 0)
+    for (int k = threadIdx.x; k <= N; k += NT) a.resid[k] = R(0);
+  ib_phase_gather<P, PAR, NT>(a, tid, nth, nband);
+  grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster, a.bar_limit_ns, nranks,
+                  a.drop_arrival && rank == nranks - 1);
+  ib_phase_interp<P, NT>(a, tid, nth, red);
+  grid_barrier<R>(a.bar, a.ctr, red, a.resid, a.cluster, a.bar_limit_ns, nranks);
+  for (int n = 1; n < N; ++n) {
+    ib_phase_jacobi<P, NT>(a, n, tid, nth, red);
+    grid_barrier<R>(a.bar, a.ctr, red, a.resid + n, a.cluster, a.bar_limit_ns, nranks);
+  }
+  ib_phase_final<P, NT>(a, tid, nth, rtid, nband, rank, nranks, red, sh);
+  grid_barrier<R>(a.bar, a.ctr, red, a.resid + N, a.cluster, a.bar_limit_ns, nranks);
+  if (rank == 0 && threadIdx.x == 0) ib_check_resid<P>(a);
+  ib_phase_moments<P, NT>(a, tid, nth, rank, nranks, sh);
+  if (a.apply) {
+    grid_barrier<R>(a.bar, a.ctr, (const R*)nullptr, (R*)nullptr, a.cluster, a.bar_limit_ns, nranks);
+    if (N > 0) ib_phase_apply<P, PAR>(a, tid, nth, nband);   // the apply reads every C_l
+  }
 }
 
 // ------------------------------------------------------------------ bodies

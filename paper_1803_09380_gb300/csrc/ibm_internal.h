@@ -125,6 +125,10 @@ struct Ctx {
   long long bar_limit_ns = kBarrierNs;       // grid-barrier wait limit (IBM_OPT_BARRIER_LIMIT_US)
   int test_drop_arrival = 0;                 // IBM_OPT_TEST_DROP_ARRIVAL
   int watchdog_steps = 0;                    // IBM_OPT_WATCHDOG_STEPS (0: off)
+  int ib_phases = 0;                         // IBM_OPT_IB_PHASES: 0 one persistent kernel, 1 phase
+                                             // kernels, 2 Jacobi iterations in one cluster
+  int ib_jc_cluster = 0;                     // CTAs of that cluster (0: not available)
+  long long nband_host = 0;                  // band nodes at the last count (sizes the phase grids)
   long long watch_due = 0;                   // steps since the last watchdog scan
 
   // CUDA graphs of one step, per parity and macro flag
@@ -163,7 +167,10 @@ inline int kernels_per_step(const Ctx& h) {
   if (h.nm > 0) {
     const int N = h.desc.n_corr;
     (void)N;
-    k += 2;                                        // correction loop, band collide+stream
+    // correction loop (one kernel; one per phase; or pre, cluster, post),
+    // band collide+stream
+    k += h.ib_phases == 1 ? h.desc.n_corr + 4
+         : (h.ib_phases == 2 && h.ib_jc_cluster >= 2 ? (h.desc.n_corr > 1 ? 4 : 3) : 2);
     if (h.nb > 0 && h.any_moving) k += 2 + 6;      // body update, marker move, band rebuild
   }
   return k;
@@ -289,6 +296,9 @@ int ib_blocks_per_sm(int prec, int threads = kIbThreads);
 // available.
 int ib_max_cluster(int prec, int threads);
 constexpr int kMaxIbCluster = 16;
+// CTAs of the cluster (of CTAs of `threads` threads) that runs the Jacobi
+// iterations of M markers (0: none).
+int jacobi_cluster_size(int prec, int M, int threads);
 void launch_body_update(const Ctx& h, cudaStream_t s);
 
 }  // namespace ibm

@@ -298,11 +298,15 @@ __device__ __forceinline__ void collide_vec(const Geom& g, const StepConsts<type
 }
 
 // Even step for the VEC nodes x0.. of row y (all inside the lattice):
-// aligned vector loads of A[i], vector stores to A[opp(i)].
+// aligned vector loads of A[i], vector stores to A[opp(i)].  A lane with
+// `skip` set (its nodes lie in a band segment, which another kernel streams)
+// loads but neither computes nor stores: its loads are issued before the
+// flag has arrived and their values are dropped.
 template <int P, bool MACRO, bool MRT>
 __device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typename Prec<P>::R>& c,
                                          typename Prec<P>::S* __restrict__ A,
-                                         typename Prec<P>::R* __restrict__ mac, int x0, int y) {
+                                         typename Prec<P>::R* __restrict__ mac, int x0, int y,
+                                         bool skip = false) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
   constexpr int VEC = VecTraits<P>::VEC;
@@ -314,6 +318,7 @@ __device__ __forceinline__ void even_vec(const Geom& g, const StepConsts<typenam
 #pragma unroll
     for (int k = 0; k < VEC; ++k) p[i][k] = Prec<P>::ldv(v.v[k], i);
   }
+  if (skip) return;
   collide_vec<P, MACRO, MRT, VEC>(g, c, p, mac, x0, y);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -447,11 +452,12 @@ __device__ __forceinline__ void k1_span(const Geom& g, const StepConsts<typename
   const int x0 = xw + lane * VEC;
   const bool flagged = MODE == K1_MAIN && x0 < g.nx && segflag[y * nseg_x + x0 / kSegW] != 0;
   if (PAR == 0) {
-    if (flagged || x0 >= g.nx) return;
+    if (x0 >= g.nx) return;
     const bool nee = has_nee(g) && (nee_column(g, x0) || nee_column(g, min(x0 + VEC, g.nx) - 1));
     if (x0 + VEC <= g.nx && !nee) {
-      even_vec<P, MACRO, MRT>(g, c, A, mac, x0, y);
+      even_vec<P, MACRO, MRT>(g, c, A, mac, x0, y, flagged);   // loads before the flag is needed
     } else {
+      if (flagged) return;
       for (int x = x0; x < g.nx && x < x0 + VEC; ++x)
         if (!nee_column(g, x)) even_node<P, MACRO, MRT>(g, c, A, mac, x, y);
     }
