@@ -50,6 +50,7 @@ SYMBOLS = ("ibm_create_lattice", "ibm_add_markers", "ibm_step", "ibm_read_fields
            "ibm_server_autotune")
 IBM_OPT_IB_CTAS, IBM_OPT_IB_THREADS = 1, 2
 IBM_OPT_WATCHDOG_STEPS, IBM_OPT_BARRIER_LIMIT_US, IBM_OPT_TEST_DROP_ARRIVAL = 3, 4, 5
+IBM_OPT_IB_PHASES = 6
 OUT_MACRO, OUT_BODIES, OUT_RESIDUAL = 1, 2, 4
 
 
