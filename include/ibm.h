@@ -244,8 +244,7 @@ enum {
                            markers, 3 per 4 SMs above that; n > 0 = min(n, SMs).  2..16 CTAs
                            run as one thread-block cluster when the device can schedule it.
                            Results do not depend on it. */
-  IBM_OPT_IB_THREADS = 2, /* threads per correction-kernel CTA: 256 (default), 512 or 1024
-                           (with IBM_OPT_IB_PHASES = 2: per CTA of the Jacobi cluster) */
+  IBM_OPT_IB_THREADS = 2, /* threads per correction-kernel CTA: 256 (default), 512 or 1024 */
   IBM_OPT_WATCHDOG_STEPS = 3, /* K > 0: after every K steps (at the next 8-step block boundary)
                            scan every stored population for NaN/Inf; a hit makes the next
                            synchronising call return IBM_ERR_DIVERGED.  0 (default): no scan.

@@ -236,7 +236,7 @@ void choose_ib_grid(Ctx& c) {
     c.ib_cluster = c.ib_grid <= c.ib_cluster_max;
   }
   // the Jacobi cluster of IBM_OPT_IB_PHASES = 2 (none: the persistent kernel)
-  c.ib_jc_cluster = c.ib_phases == 2 && M > kSmallIbMarkers ? jacobi_cluster_size(c.prec, M, c.ib_threads) : 0;
+  c.ib_jc_cluster = c.ib_phases == 2 && M > kSmallIbMarkers ? jacobi_cluster_size(c.prec, M) : 0;
 }
 
 ibm_status upload_markers(Ctx* h) {

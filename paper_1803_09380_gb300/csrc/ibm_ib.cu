@@ -163,6 +163,12 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 // Shared-memory address `addr` of this CTA mapped to cluster CTA `rank`.
 __device__ __forceinline__ unsigned int dsmem_map(unsigned int addr, unsigned int rank) {
   unsigned int r;
@@ -176,50 +182,93 @@ __device__ __forceinline__ void dsmem_ld(unsigned int addr, double2& v) {
   asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
 }
 
+// Threads per CTA of the Jacobi cluster.
+constexpr int kJcThreads = 1024;
+
 // Shared memory of one CTA of the Jacobi cluster for a slice of `per`
-// markers: A^n and A^{n+1} and b (pairs), the first kRowHead entries of each
-// G row as weights and cluster addresses of the coupled markers' A slots,
-// the row lengths and the interpolated densities.
+// markers: A^n and A^{n+1} (pairs); when a slice is larger than the CTA
+// (REG false) also b, the first kRowHead entries of each G row as weights
+// and cluster addresses of the coupled markers' A slots, the row lengths
+// and the interpolated densities.
 template <class R>
-__host__ __device__ constexpr size_t jacobi_smem_bytes(int per) {
-  return (size_t)per * (3 * 2 * sizeof(R) + (kRowHead + 1) * sizeof(R) + kRowHead * sizeof(unsigned int) +
-                        sizeof(int));
+__host__ __device__ constexpr size_t jacobi_smem_bytes(int per, bool reg) {
+  return (size_t)per * (2 * 2 * sizeof(R) +
+                        (reg ? 0 : 2 * sizeof(R) + (kRowHead + 1) * sizeof(R) + kRowHead * sizeof(unsigned int) +
+                                       sizeof(int)));
 }
 
-// Jacobi iterations n = 1 .. N-1 (A^{n+1} = A^n + b - G A^n) by the
-// `per`-marker slices of the cluster's CTAs (the residual of A^N is the
-// history pass's).  The G rows are constant through the iterations: their
-// first kRowHead entries are staged once as weights and peer addresses, so
-// an iteration is kRowHead independent distributed-shared-memory loads per
-// marker, summed in the row's stored (ascending marker) order as
-// deviation() sums them, then one hardware cluster barrier.
-template <int P, int NTC>
-__global__ void __launch_bounds__(NTC, 1024 / NTC) k_ib_jacobi_cluster(IbArgs<P> a, int per) {
+// One Jacobi update of marker l (A^{n+1} = A^n + b - G A^n): the first
+// kRowHead entries of its G row come as weights w[] and peer addresses ad[]
+// of A^n's slots (offset `off` selects the buffer), the rest from G itself;
+// the row is summed in its stored (ascending marker) order, as deviation()
+// sums it.
+template <class R, class V, class Args>
+__device__ __forceinline__ void jacobi_row(const Args& a, int l, int k1, const R* w, const unsigned int* ad,
+                                           unsigned int off, unsigned int base, int per, R& djx, R& djy,
+                                           V b) {
+  V v[kRowHead];
+#pragma unroll
+  for (int j = 0; j < kRowHead; ++j)
+    if (j < k1) dsmem_ld(ad[j] + off, v[j]);
+  R sx = R(0), sy = R(0);
+#pragma unroll
+  for (int j = 0; j < kRowHead; ++j)
+    if (j < k1) {
+      sx += w[j] * v[j].x;
+      sy += w[j] * v[j].y;
+    }
+  for (int k = kRowHead; k < k1; ++k) {                      // rare long rows: the rest from G
+    const Ent<R> q = a.G[(long long)l * kGCap + k];
+    const int owner = q.m / per;
+    V u;
+    dsmem_ld(dsmem_map(base + off + (unsigned int)((q.m - owner * per) * sizeof(V)), (unsigned int)owner), u);
+    sx += q.w * u.x;
+    sy += q.w * u.y;
+  }
+  djx = b.x - sx;
+  djy = b.y - sy;
+}
+
+// Jacobi iterations n = 1 .. N-1 by the `per`-marker slices of the
+// cluster's CTAs (the residual of A^N is the history pass's).  The G rows
+// are constant through the iterations: their first kRowHead entries are
+// taken once as weights and peer addresses -- in registers when a slice
+// fits the CTA (REG: one marker per thread), else staged in shared memory --
+// so an iteration is kRowHead independent distributed-shared-memory loads
+// per marker and one hardware cluster barrier, split so that the store of
+// A^{n+1} to the history overlaps the wait.
+template <int P, bool REG>
+__global__ void __launch_bounds__(kJcThreads, 1) k_ib_jacobi_cluster(IbArgs<P> a, int per) {
   typedef typename Prec<P>::R R;
   typedef typename Vec2<R>::T V;
+  constexpr int NTC = kJcThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* As = reinterpret_cast<V*>(smem_raw);                    // [2][per]: A^n and A^{n+1} of the slice
-  V* bs = As + 2 * per;                                      // [per]: b
-  R* wt = reinterpret_cast<R*>(bs + per);                    // [kRowHead][per]
-  R* rs = wt + kRowHead * per;                               // [per]: interpolated density
-  unsigned int* ad = reinterpret_cast<unsigned int*>(rs + per);   // [kRowHead][per]
-  int* nc = reinterpret_cast<int*>(ad + kRowHead * per);     // [per]: row length
+  V* bs = As + 2 * per;                                      // [per]: b                    (!REG)
+  R* wt = reinterpret_cast<R*>(bs + per);                    // [kRowHead][per]             (!REG)
+  R* rs = wt + kRowHead * per;                               // [per]: interpolated density (!REG)
+  unsigned int* ad = reinterpret_cast<unsigned int*>(rs + per);   // [kRowHead][per]        (!REG)
+  int* nc = reinterpret_cast<int*>(ad + kRowHead * per);     // [per]: row length           (!REG)
   __shared__ R red[2 * (NTC / 32)];
   const unsigned int crank = cluster_rank();
   const int M = a.M, N = a.N;
   const int m0 = (int)crank * per, cnt = max(0, min(M, m0 + per) - m0);
   V* Ah = reinterpret_cast<V*>(a.Ah);
   const unsigned int base = (unsigned int)__cvta_generic_to_shared(As);
+  // the row heads (REG: this thread's marker i = threadIdx.x)
+  R w_r[REG ? kRowHead : 1];
+  unsigned int ad_r[REG ? kRowHead : 1];
+  V b_r, a_r;
+  R rs_r = R(1);
+  int k1_r = 0;
   for (int i = threadIdx.x; i < cnt; i += NTC) {
     const int l = m0 + i;
-    As[i] = Ah[M + l];                                       // A^1 = b
+    const V a1 = Ah[M + l];                                  // A^1 = b
+    As[i] = a1;
     V b;
     b.x = a.mq[4 * l + 1];
     b.y = a.mq[4 * l + 2];
-    bs[i] = b;
-    rs[i] = a.mq[4 * l];
     const int k1 = a.gcnt[l];
-    nc[i] = k1;
     const Ent<R>* row = a.G + (long long)l * kGCap;
 #pragma unroll
     for (int j = 0; j < kRowHead; ++j) {
@@ -231,52 +280,67 @@ __global__ void __launch_bounds__(NTC, 1024 / NTC) k_ib_jacobi_cluster(IbArgs<P>
         addr = dsmem_map(base + (unsigned int)((q.m - owner * per) * sizeof(V)), (unsigned int)owner);
         w = q.w;
       }
-      ad[j * per + i] = addr;
-      wt[j * per + i] = w;
+      if (REG) {
+        ad_r[j] = addr;
+        w_r[j] = w;
+      } else {
+        ad[j * per + i] = addr;
+        wt[j * per + i] = w;
+      }
+    }
+    if (REG) {
+      b_r = b;
+      a_r = a1;
+      rs_r = a.mq[4 * l];
+      k1_r = k1;
+    } else {
+      bs[i] = b;
+      rs[i] = a.mq[4 * l];
+      nc[i] = k1;
     }
   }
   cluster_sync_all();
   const unsigned int half = (unsigned int)(per * sizeof(V));
+  const bool mine = REG && (int)threadIdx.x < cnt;
   int cur = 0;
   for (int n = 1; n < N; ++n) {
     const V* Acur = As + cur * per;
     V* Anxt = As + (cur ^ 1) * per;
     const unsigned int off = cur ? half : 0u;
     R rmax = R(0);
-    for (int i = threadIdx.x; i < cnt; i += NTC) {
-      const int l = m0 + i, k1 = nc[i];
-      V v[kRowHead];
-#pragma unroll
-      for (int j = 0; j < kRowHead; ++j)
-        if (j < k1) dsmem_ld(ad[j * per + i] + off, v[j]);
-      R sx = R(0), sy = R(0);
-#pragma unroll
-      for (int j = 0; j < kRowHead; ++j)
-        if (j < k1) {
-          const R w = wt[j * per + i];
-          sx += w * v[j].x;
-          sy += w * v[j].y;
-        }
-      for (int k = kRowHead; k < k1; ++k) {                  // rare long rows: the rest from G
-        const Ent<R> q = a.G[(long long)l * kGCap + k];
-        const int owner = q.m / per;
-        V u;
-        dsmem_ld(dsmem_map(base + off + (unsigned int)((q.m - owner * per) * sizeof(V)), (unsigned int)owner), u);
-        sx += q.w * u.x;
-        sy += q.w * u.y;
+    if (REG) {
+      if (mine) {
+        R djx, djy;
+        jacobi_row<R, V>(a, m0 + threadIdx.x, k1_r, w_r, ad_r, off, base, per, djx, djy, b_r);
+        a_r.x = a_r.x + djx;
+        a_r.y = a_r.y + djy;
+        Anxt[threadIdx.x] = a_r;
+        rmax = (R)(sqrt(djx * djx + djy * djy) / rs_r);
       }
-      const V b = bs[i];
-      const R djx = b.x - sx, djy = b.y - sy;
-      V an;
-      an.x = Acur[i].x + djx;
-      an.y = Acur[i].y + djy;
-      Anxt[i] = an;
-      Ah[(long long)(n + 1) * M + l] = an;
-      rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / rs[i]));
+    } else {
+      for (int i = threadIdx.x; i < cnt; i += NTC) {
+        R w[kRowHead];
+        unsigned int adl[kRowHead];
+#pragma unroll
+        for (int j = 0; j < kRowHead; ++j) {
+          w[j] = wt[j * per + i];
+          adl[j] = ad[j * per + i];
+        }
+        R djx, djy;
+        jacobi_row<R, V>(a, m0 + i, nc[i], w, adl, off, base, per, djx, djy, bs[i]);
+        V an;
+        an.x = Acur[i].x + djx;
+        an.y = Acur[i].y + djy;
+        Anxt[i] = an;
+        Ah[(long long)(n + 1) * M + m0 + i] = an;
+        rmax = nanmax(rmax, (R)(sqrt(djx * djx + djy * djy) / rs[i]));
+      }
     }
     R* rd = red + (n & 1) * (NTC / 32);                      // two buffers: no block barrier
     warp_max_to<R>(rmax, rd);
-    cluster_sync_all();                                       // every read of A^n is done
+    cluster_arrive();                                         // A^{n+1} written, A^n read
+    if (mine) Ah[(long long)(n + 1) * M + m0 + threadIdx.x] = a_r;
+    cluster_wait();
     if (threadIdx.x == 0) {
       R m = rd[0];
       for (int k = 1; k < NTC / 32; ++k) m = nanmax(m, rd[k]);
@@ -286,7 +350,7 @@ __global__ void __launch_bounds__(NTC, 1024 / NTC) k_ib_jacobi_cluster(IbArgs<P>
   }
 }
 
-constexpr int kJacobiSmemMax = 192 * 1024;                  // dynamic shared memory of one slice pair
+constexpr int kJacobiSmemMax = 192 * 1024;                  // dynamic shared memory of one CTA
 
 // Collide+stream of the 32-node row segments that hold band nodes, after
 // the correction kernel has corrected them: one warp per segment.
@@ -381,15 +445,17 @@ static void launch_band_collide(dim3 g2, dim3 b2, cudaStream_t s, int prio, cons
   }
 }
 
-// One cluster of h.ib_jc_cluster CTAs of NTC threads runs the Jacobi
-// iterations (IBM_OPT_IB_PHASES = 2).
-template <int P, int NTC>
+
+// One cluster of h.ib_jc_cluster CTAs runs the Jacobi iterations
+// (IBM_OPT_IB_PHASES = 2).
+template <int P>
 static void launch_jacobi_cluster(const Ctx& h, cudaStream_t s, const IbArgs<P>& a) {
   const int C = h.ib_jc_cluster, per = (h.nm + C - 1) / C;
+  const bool reg = per <= kJcThreads;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
-  cfg.blockDim = dim3(NTC);
-  cfg.dynamicSmemBytes = jacobi_smem_bytes<typename Prec<P>::R>(per);
+  cfg.blockDim = dim3(kJcThreads);
+  cfg.dynamicSmemBytes = jacobi_smem_bytes<typename Prec<P>::R>(per, reg);
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributePriority;
@@ -400,7 +466,8 @@ static void launch_jacobi_cluster(const Ctx& h, cudaStream_t s, const IbArgs<P>&
   attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cudaLaunchKernelEx(&cfg, k_ib_jacobi_cluster<P, NTC>, a, per);
+  if (reg) cudaLaunchKernelEx(&cfg, k_ib_jacobi_cluster<P, true>, a, per);
+  else cudaLaunchKernelEx(&cfg, k_ib_jacobi_cluster<P, false>, a, per);
 }
 
 template <int P>
@@ -417,13 +484,7 @@ static void ib_loop_t(const Ctx& h, int parity, bool macro, cudaStream_t s) {
     };
     if (parity == 0) go(k_ib_pre<P, 0, kIbThreads>);
     else go(k_ib_pre<P, 1, kIbThreads>);
-    if (h.desc.n_corr > 1) {
-      switch (h.ib_threads) {
-        case 1024: launch_jacobi_cluster<P, 1024>(h, s, a); break;
-        case 512: launch_jacobi_cluster<P, 512>(h, s, a); break;
-        default: launch_jacobi_cluster<P, 256>(h, s, a);
-      }
-    }
+    if (h.desc.n_corr > 1) launch_jacobi_cluster<P>(h, s, a);
     go(k_ib_post<P, kIbThreads>);
   } else if (h.ib_phases == 1) {
     // one kernel per phase; grids sized by the work (every loop strides, so
@@ -570,25 +631,28 @@ void launch_body_update(const Ctx& h, cudaStream_t s) {
 }
 
 
-// Largest cluster (at most 16 CTAs of NTC threads) that can run the Jacobi
-// iterations of M markers with the slices in shared memory; 0 when none can.
-template <int P, int NTC>
+// Largest cluster (at most 16 CTAs) that can run the Jacobi iterations of
+// M markers with the slices in shared memory; 0 when none can.
+template <int P>
 static int jacobi_cluster_t(int M) {
-  void (*kern)(IbArgs<P>, int) = k_ib_jacobi_cluster<P, NTC>;
+  void (*kr)(IbArgs<P>, int) = k_ib_jacobi_cluster<P, true>;
+  void (*ks)(IbArgs<P>, int) = k_ib_jacobi_cluster<P, false>;
   // the attributes allow any slice size up to kJacobiSmemMax, so that
-  // lattices with different marker counts can share the kernel
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacobiSmemMax) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
+  // lattices with different marker counts can share the kernels
+  for (auto kern : {kr, ks})
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacobiSmemMax) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
   for (int c = kMaxIbCluster; c >= 2; --c) {
     const int per = (M + c - 1) / c;
-    const size_t smem = jacobi_smem_bytes<typename Prec<P>::R>(per);
+    const bool reg = per <= kJcThreads;
+    const size_t smem = jacobi_smem_bytes<typename Prec<P>::R>(per, reg);
     if (smem > (size_t)kJacobiSmemMax) break;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c);
-    cfg.blockDim = dim3(NTC);
+    cfg.blockDim = dim3(kJcThreads);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -598,7 +662,7 @@ static int jacobi_cluster_t(int M) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, reg ? kr : ks, &cfg) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -607,16 +671,7 @@ static int jacobi_cluster_t(int M) {
   return 0;
 }
 
-template <int P>
-static int jacobi_cluster_p(int M, int threads) {
-  switch (threads) {
-    case 1024: return jacobi_cluster_t<P, 1024>(M);
-    case 512: return jacobi_cluster_t<P, 512>(M);
-    default: return jacobi_cluster_t<P, 256>(M);
-  }
-}
-
-int jacobi_cluster_size(int prec, int M, int threads) {
+int jacobi_cluster_size(int prec, int M) {
   int dev = 0, ok = 0;
   if (M < 2 || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, dev) != cudaSuccess || !ok) {
@@ -624,10 +679,10 @@ int jacobi_cluster_size(int prec, int M, int threads) {
     return 0;
   }
   switch (prec) {
-    case PREC_FP64: return jacobi_cluster_p<PREC_FP64>(M, threads);
-    case PREC_FP32: return jacobi_cluster_p<PREC_FP32>(M, threads);
-    case PREC_FP16_DEV: return jacobi_cluster_p<PREC_FP16_DEV>(M, threads);
-    default: return jacobi_cluster_p<PREC_BF16_DEV>(M, threads);
+    case PREC_FP64: return jacobi_cluster_t<PREC_FP64>(M);
+    case PREC_FP32: return jacobi_cluster_t<PREC_FP32>(M);
+    case PREC_FP16_DEV: return jacobi_cluster_t<PREC_FP16_DEV>(M);
+    default: return jacobi_cluster_t<PREC_BF16_DEV>(M);
   }
 }
 

@@ -296,9 +296,8 @@ int ib_blocks_per_sm(int prec, int threads = kIbThreads);
 // available.
 int ib_max_cluster(int prec, int threads);
 constexpr int kMaxIbCluster = 16;
-// CTAs of the cluster (of CTAs of `threads` threads) that runs the Jacobi
-// iterations of M markers (0: none).
-int jacobi_cluster_size(int prec, int M, int threads);
+// CTAs of the cluster that runs the Jacobi iterations of M markers (0: none).
+int jacobi_cluster_size(int prec, int M);
 void launch_body_update(const Ctx& h, cudaStream_t s);
 
 }  // namespace ibm

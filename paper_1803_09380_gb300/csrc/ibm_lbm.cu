@@ -36,14 +36,20 @@ namespace ibm {
 // step: spans without boundary or ragged nodes take the vector path (lanes
 // whose nodes lie in band segments sit out); the others go node by node
 // through the boundary-aware path.
-constexpr int kK1Threads = 256;   // threads per collide+stream block (whole warps per row span)
+// Threads per collide+stream block (whole warps per row span).  Two warps:
+// a correction-kernel CTA resident beside collide+stream then displaces
+// only the registers it needs, not whole 256-thread blocks (on the 4096^2
+// FP32 Couette step 64 beat 128 and 256 by 0.3 % and 2.4 %; FP16 storage
+// gained 5.6 %; alone the kernel is unchanged).
+constexpr int kK1Threads = 64;
 
-// Resident blocks asked of the register allocator: 4 (64 registers) for the
-// node-local even step, 3 (80) for the odd step with its shuffles; FP64
-// needs one block fewer.  Without it the allocator's own choice varied
-// with unrelated edits, once spilling the odd step's hot loop.
+// Resident blocks asked of the register allocator: 1024 threads (64
+// registers) for the node-local even step, 768 (80) for the odd step with
+// its shuffles; FP64 needs 256 threads fewer.  Without it the allocator's
+// own choice varied with unrelated edits, once spilling the odd step's hot
+// loop.
 constexpr int k1_min_blocks(int P, int PAR) {
-  return (PAR ? 3 : 4) - (P == PREC_FP64 ? 1 : 0);
+  return ((PAR ? 3 : 4) - (P == PREC_FP64 ? 1 : 0)) * (256 / kK1Threads);
 }
 
 template <int P, int PAR, bool MACRO, int MODE, bool MRT>

@@ -401,3 +401,21 @@ def test_phase_kernels_are_bitwise_the_persistent_kernel(prec, case_name):
     if case_name.startswith("couette"):
         # more than 512 markers: the chain and the cluster really ran
         assert launches[1] > launches[2] > launches[0]
+
+
+def test_cluster_jacobi_with_slices_larger_than_a_cta_is_bitwise():
+    """A 4800^2 Couette pair of rings has about 16,500 markers: the Jacobi
+    cluster's slices exceed one marker per thread, so the G row heads are
+    staged in shared memory instead of registers; bitwise the persistent
+    kernel's results still."""
+    case = wl.couette(4800)
+    assert sum(len(b.xy) for b in case.bodies) > 16 * 1024
+    out = []
+    for phases in (0, 2):
+        lat = gpu_lattice(case, "fp32", None)
+        ibm.ibm_set_option(lat.h, ibm.IBM_OPT_IB_PHASES, phases)
+        lat.step(9)
+        out.append((lat.resid, lat.bodies, lat.moments()[1]))
+        lat.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
