@@ -295,9 +295,9 @@ def run_reference(args, rank, world):
 # sources the capture ran; the figure is reported only while the sources
 # still hash to that value.
 TRAFFIC = {
-    ("fp32", 4096): (1139.8e6, "62a14777a1211814"),
-    ("fp16", 4096): (542.8e6, "62a14777a1211814"),
-    ("fp64", 4096): (2314.4e6, "62a14777a1211814"),
+    ("fp32", 4096): (1141.1e6, "3e99c95b0c6971f9"),
+    ("fp16", 4096): (541.5e6, "3e99c95b0c6971f9"),
+    ("fp64", 4096): (2313.4e6, "3e99c95b0c6971f9"),
 }
 KERNEL_SOURCES = ("ibm_k1.cuh", "ibm_lbm.cu", "ibm_device.cuh")
 
