@@ -425,7 +425,7 @@ const char *ibm_server_last_error(ibm_server s);
  *   force_out  2 doubles, the force on all markers together (may be NULL).
  * The work runs on cuda_stream (NULL: the legacy default stream) on the
  * current device as one CTA per kernel, and the call returns after
- * synchronising that stream.  On entry it clears the calling thread's
+ * synchronising that stream, so it cannot be captured into a CUDA graph.  On entry it clears the calling thread's
  * pending CUDA launch error (left by earlier work), so that it reports only
  * errors of its own work.  When the call fails, the contents of f, resid_out
  * and force_out are undefined.
@@ -436,8 +436,7 @@ const char *ibm_server_last_error(ibm_server s);
  * nx * ny <= 262144, 1 <= n <= 512 markers, 0 <= n_corr <= 64; larger
  * requests return IBM_ERR_INVALID with a message in ibm_last_error(NULL).
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture
- * begins.  All calls share the array and it keeps the last call's contents
+ * (cudaGetSymbolAddress).  All calls share the array and it keeps the last call's contents
  * (the call clears what must start empty); calls that overlap on the GPU --
  * from several host threads or streams at once -- race and give wrong
  * results. */
