@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define IBM_ABI_VERSION 4
+#define IBM_ABI_VERSION 5
 
 typedef struct ibm_ctx *ibm_handle; /* opaque, library-owned */
 
@@ -146,7 +146,17 @@ enum {
   IBM_FIELD_BODIES = 5,       /* [nbodies][9]: xc, yc, ux, uy, omega, theta, Fx, Fy, T */
   IBM_FIELD_RESIDUAL = 6,     /* [n_corr + 1]: r^0..r^N of the last step */
   IBM_FIELD_MARKERS = 7,      /* [nmarkers][2]: current marker positions */
-  IBM_FIELD_MACRO_INIT = 8    /* write only, [3][ny][nx] rho, ux, uy: f := f^eq(rho, u) */
+  IBM_FIELD_MACRO_INIT = 8,   /* write only, [3][ny][nx] rho, ux, uy: f := f^eq(rho, u) */
+  IBM_FIELD_BODY_STATE = 9    /* read/write, [nbodies][9]: xc, yc, ux, uy, omega, theta of the
+                                 body (Eqs. 40-42) and its ux, uy, omega of the step before,
+                                 which the internal-mass terms of Eqs. 37-38 use.  Writing it
+                                 moves the body's markers rigidly to the new pose (marker
+                                 velocities u + omega x r) and rebuilds the band before the
+                                 next step; IBM_FIELD_F plus IBM_FIELD_BODY_STATE are a
+                                 complete checkpoint: a lattice created with the same
+                                 parameters and bodies and given both continues bit for bit
+                                 with FP64 and FP32 storage (16-bit storage: to the storage
+                                 rounding of the populations) */
 };
 
 /* Flags for ibm_step. */
@@ -192,13 +202,19 @@ ibm_status ibm_step(ibm_handle h, int nsteps, unsigned flags);
  * with the force and torque of Eq. 29 and Eq. 38 of the last step (BODIES),
  * the no-slip residuals r^0..r^N of the correction loop of section 2.3
  * (RESIDUAL; returns IBM_WARN_NOT_CONVERGED when corr_tol > 0 and r^N is
- * above it) and the marker positions X_l (MARKERS).  Errors: IBM_ERR_INVALID
+ * above it), the marker positions X_l (MARKERS) and the body state needed to
+ * resume a run (BODY_STATE).  Errors: IBM_ERR_INVALID
  * for an unknown field or a wrong n_elems, and the device errors of
  * ibm_sync. */
 ibm_status ibm_read_fields(ibm_handle h, int field, double *host_dst, size_t n_elems);
 
-/* Writes IBM_FIELD_F (raw post-stream populations) or IBM_FIELD_MACRO_INIT
- * (equilibrium of the given rho, u) from host_src, n_elems doubles. */
+/* Writes IBM_FIELD_F (raw post-stream populations of Eq. 1),
+ * IBM_FIELD_MACRO_INIT (the equilibrium of Eq. 3 at the given rho, u) or
+ * IBM_FIELD_BODY_STATE (the pose and velocities of Eqs. 40-42, see the field
+ * list) from host_src, n_elems doubles, and synchronises the handle's
+ * stream.  Errors: IBM_ERR_INVALID for a field that cannot be written, a
+ * wrong n_elems or a non-finite value (and a density <= 0 for
+ * MACRO_INIT), and the device errors of ibm_sync. */
 ibm_status ibm_write_fields(ibm_handle h, int field, const double *host_src, size_t n_elems);
 
 /* Blocks until the handle's queued work is done; reports device errors:

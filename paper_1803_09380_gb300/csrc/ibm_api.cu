@@ -823,6 +823,21 @@ ibm_status ibm_read_fields(ibm_handle h, int field, double* host_dst, size_t n_e
         }
         return IBM_OK;
       }
+      case IBM_FIELD_BODY_STATE: {
+        if (n_elems != (size_t)9 * c.nb) return fail(h, IBM_ERR_INVALID, "n_elems must be 9*nbodies");
+        std::vector<BodyDev> bd(c.nb);
+        if (c.nb)
+          IBM_CK(h, cudaMemcpyAsync(bd.data(), c.dbodies, sizeof(BodyDev) * c.nb, cudaMemcpyDeviceToHost,
+                                    c.stream));
+        IBM_CK(h, cudaStreamSynchronize(c.stream));
+        for (int b = 0; b < c.nb; ++b) {
+          double* o = host_dst + 9 * b;
+          o[0] = bd[b].xc[0]; o[1] = bd[b].xc[1]; o[2] = bd[b].u[0]; o[3] = bd[b].u[1];
+          o[4] = bd[b].omega; o[5] = bd[b].theta; o[6] = bd[b].u_prev[0]; o[7] = bd[b].u_prev[1];
+          o[8] = bd[b].omega_prev;
+        }
+        return IBM_OK;
+      }
       case IBM_FIELD_RESIDUAL: {
         const int N = c.desc.n_corr;
         if (n_elems != (size_t)N + 1) return fail(h, IBM_ERR_INVALID, "n_elems must be n_corr+1");
@@ -885,6 +900,29 @@ ibm_status ibm_write_fields(ibm_handle h, int field, const double* host_src, siz
       IBM_CK(h, cudaMemcpyAsync(c.dio, host_src, 8 * 3 * n, cudaMemcpyHostToDevice, c.stream));
       launch_fields(c, FIELD_OP_INIT_EQ, c.dio, nullptr, c.stream);
       c.parity = 0;
+    } else if (field == IBM_FIELD_BODY_STATE) {
+      if (n_elems != (size_t)9 * c.nb) return fail(h, IBM_ERR_INVALID, "n_elems must be 9*nbodies");
+      for (size_t k = 0; k < n_elems; ++k)
+        if (!is_finite(host_src[k])) return fail(h, IBM_ERR_INVALID, "body state must be finite");
+      if (c.nb == 0) return IBM_OK;
+      // the rest of each record (kind, marker range, mass properties,
+      // reference angle, last forces) stays as it is on the device
+      std::vector<BodyDev> bd(c.nb);
+      IBM_CK(h, cudaMemcpyAsync(bd.data(), c.dbodies, sizeof(BodyDev) * c.nb, cudaMemcpyDeviceToHost, c.stream));
+      IBM_CK(h, cudaStreamSynchronize(c.stream));
+      for (int b = 0; b < c.nb; ++b) {
+        const double* v = host_src + 9 * b;
+        bd[b].xc[0] = v[0]; bd[b].xc[1] = v[1]; bd[b].u[0] = v[2]; bd[b].u[1] = v[3];
+        bd[b].omega = v[4]; bd[b].theta = v[5]; bd[b].u_prev[0] = v[6]; bd[b].u_prev[1] = v[7];
+        bd[b].omega_prev = v[8];
+      }
+      IBM_CK(h, cudaMemcpyAsync(c.dbodies, bd.data(), sizeof(BodyDev) * c.nb, cudaMemcpyHostToDevice, c.stream));
+      IBM_CK(h, cudaStreamSynchronize(c.stream));
+      // markers to the new pose; the band follows them before the next step
+      if (c.any_moving && c.nm > 0) {
+        launch_marker_move(c, c.stream);
+        c.band_valid = false;
+      }
     } else {
       return fail(h, IBM_ERR_INVALID, "field is not writable");
     }

@@ -630,6 +630,16 @@ void launch_body_update(const Ctx& h, cudaStream_t s) {
   else body_update_t<float>(h, s);
 }
 
+void launch_marker_move(const Ctx& h, cudaStream_t s) {
+  if (h.nm == 0 || !h.any_moving) return;
+  if (h.r_bytes == 8)
+    k_marker_move<double><<<blocks_for(h.nm, 128), 128, 0, s>>>(h.nm, h.dbodies, h.dmbody, h.ddX, h.ddY, h.dX,
+                                                                 h.dY, (double*)h.dUx, (double*)h.dUy);
+  else
+    k_marker_move<float><<<blocks_for(h.nm, 128), 128, 0, s>>>(h.nm, h.dbodies, h.dmbody, h.ddX, h.ddY, h.dX,
+                                                                h.dY, (float*)h.dUx, (float*)h.dUy);
+}
+
 
 // Largest cluster (at most 16 CTAs) that can run the Jacobi iterations of
 // M markers with the slices in shared memory; 0 when none can.

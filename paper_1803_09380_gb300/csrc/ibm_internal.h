@@ -299,5 +299,7 @@ constexpr int kMaxIbCluster = 16;
 // CTAs of the cluster that runs the Jacobi iterations of M markers (0: none).
 int jacobi_cluster_size(int prec, int M);
 void launch_body_update(const Ctx& h, cudaStream_t s);
+// Rigid motion of every moving body's markers to its current pose (Eqs. 41-42).
+void launch_marker_move(const Ctx& h, cudaStream_t s);
 
 }  // namespace ibm

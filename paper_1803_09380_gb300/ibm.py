@@ -32,6 +32,7 @@ COLL_BGK, COLL_MRT = 0, 1
 PAPER_MRT_RATES = (1.1, 1.25, 1.8)   # s_e, s_eps, s_q of section 3
 FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_F = 1, 2, 3, 4
 FIELD_BODIES, FIELD_RESIDUAL, FIELD_MARKERS, FIELD_MACRO_INIT = 5, 6, 7, 8
+FIELD_BODY_STATE = 9
 STEP_DEFAULT, STEP_NO_GRAPH, STEP_TIME_KERNELS, STEP_NO_MACRO = 0, 1, 2, 4
 
 PRECISIONS = {"fp64": IBM_FP64, "fp32": IBM_FP32, "fp16": IBM_FP16_DEV, "bf16": IBM_BF16_DEV}
@@ -279,7 +280,7 @@ def _field_shape(h, field, nx, ny, n_corr):
     if field == FIELD_RESIDUAL:
         return (n_corr + 1,)
     _, m, b, _, _ = ibm_get_sizes(h)
-    if field == FIELD_BODIES:
+    if field in (FIELD_BODIES, FIELD_BODY_STATE):
         return (b, 9)
     if field == FIELD_MARKERS:
         return (m, 2)
@@ -622,6 +623,16 @@ class Lattice:
     @property
     def markers(self):
         return self.read(FIELD_MARKERS)
+
+    def checkpoint(self) -> dict:
+        """Everything a lattice made with the same parameters and bodies needs
+        to continue this run bit for bit: the populations and the bodies'
+        pose and velocities (current and previous step)."""
+        return {"f": self.read(FIELD_F), "body_state": self.read(FIELD_BODY_STATE)}
+
+    def restore(self, state: dict) -> None:
+        self.write(FIELD_F, state["f"])
+        self.write(FIELD_BODY_STATE, state["body_state"])
 
     def init_equilibrium(self, rho, ux, uy):
         shp = (self.ny, self.nx)
