@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--serve-steps", type=int, default=500)
     p.add_argument("--serve-prec", choices=list(BYTES_PER_POP), default="fp32")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
-    p.add_argument("--serve-active", type=int, default=32, help="cases resident at once")
+    p.add_argument("--serve-active", type=int, default=128, help="cases resident at once")
     return p.parse_args()
 
 
@@ -485,9 +485,9 @@ def run_serving(args, local_rank):
                   "seed 1803",
            "solve": f"{args.serve_steps} time steps of the case, residual history read back"}
 
-    def serve(max_active, paced, batched=False, tune=False):
+    def serve(max_active, paced, batched=False, tune=False, prec=prec, preset=None):
         with ibm.Server(device=local_rank, max_active=max_active, steps_per_launch=16,
-                        batched=batched) as srv:
+                        batched=batched, **(preset or {})) as srv:
             tuned = None
             if tune:
                 # the autotuner times tile size, markers per correction CTA and
@@ -523,9 +523,23 @@ def run_serving(args, local_rank):
                 "p99_ms": st["p99_ms"], "mlups": st["mlups"], "failed": st["failed"],
                 "max_active": args.serve_active, "wall_s": wall, "autotuned": tuned,
                 "host_admit_s": st["host_admit_s"], "host_launch_s": st["host_launch_s"]})
-    stp, wallp, _ = serve(args.serve_active, True)
+    if prec == "fp32":
+        # the same stream with FP16 deviation storage, batched, with the
+        # parameters the autotuner chose for FP32
+        preset = {"tile_nodes": tuned["tile_nodes"], "corr_first": tuned["corr_first"],
+                  "ib_markers_per_cta": tuned["markers_per_cta"]}
+        sth, wallh, _ = serve(args.serve_active, True, batched=True, prec="fp16", preset=preset)
+        out["fp16_storage"] = {"solves_per_s": sth["solves_per_s"], "p50_ms": sth["p50_ms"],
+                               "p99_ms": sth["p99_ms"], "failed": sth["failed"], "wall_s": wallh,
+                               "vs_fp32_batched": sth["solves_per_s"] / st["solves_per_s"],
+                               "what": "batched server, FP16 deviation storage, the FP32 run's tuned parameters"}
+    # per-case streams peak at about 64 resident cases (more streams than
+    # that cost more than they overlap)
+    active_s = min(args.serve_active, 64)
+    stp, wallp, _ = serve(active_s, True)
     out["per_case_streams"] = {"solves_per_s": stp["solves_per_s"], "p50_ms": stp["p50_ms"],
                                "p99_ms": stp["p99_ms"], "failed": stp["failed"], "wall_s": wallp,
+                               "max_active": active_s,
                                "what": "each resident case stepped by its own graph launches on its own stream"}
     wall_l = lattice_one_at_a_time()
     out["solves_per_s_one_at_a_time"] = len(stream) / wall_l

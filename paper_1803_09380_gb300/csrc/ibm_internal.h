@@ -64,6 +64,9 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaMemPool_t pool = nullptr;  // set: stream-ordered allocations from this pool
+  char* chunk_ptr = nullptr;      // pool mode: free part of the current small-allocation chunk
+  size_t chunk_left = 0;
+  std::vector<void*> chunks;      // pool mode: the chunks, released with the lattice
   cudaStream_t ib_stream = nullptr;   // high-priority stream of the correction loop
   int ib_prio = 0;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

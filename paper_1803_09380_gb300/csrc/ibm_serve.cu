@@ -109,7 +109,7 @@ double case_bytes(const ibm_lattice_desc& d, int M, int nb) {
   b += M * 2.0 * r * (d.n_corr + 1);
   b += bcap * (8 + kBandCap * ent + 8 * r + 4);
   b += nb * (sizeof(ibm::BodyDev) + 24.0 * (M / kForceChunk + 1));
-  return b + (1 << 20);
+  return b + (1 << 20) + 2.0 * (16 << 20);                  // + the unused part of two 16 MiB chunks
 }
 
 // Correction-loop CTAs of a served case: one CTA per `per_cta` markers, at
