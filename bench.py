@@ -235,7 +235,9 @@ def cpu_baseline(args):
 
 
 def cpu_sample_set(args):
-    """The oracle on the survey's sample set, one thread and all cores."""
+    """The oracle, one thread and all cores, on a fixed sample set: the
+    64^2 ring case in full, the 1024^2 and 4096^2 Couette lattices and the
+    1600 x 800 cylinder channel for 100 steps each."""
     import oracle
     from paper_1803_09380_gb300 import workloads as wl
     cases = [("ring 64x64 (radii 10, 25), 5000 steps", wl.couette_64(), 5000),
