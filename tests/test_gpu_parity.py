@@ -419,3 +419,21 @@ def test_cluster_jacobi_with_slices_larger_than_a_cta_is_bitwise():
         lat.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n_corr", [0, 1, 2])
+def test_cluster_jacobi_form_with_few_iterations_is_bitwise(n_corr):
+    """Degenerate iteration counts of the Jacobi-cluster form: with N <= 1
+    no cluster is launched (the two persistent kernels do the whole loop),
+    with N = 2 the cluster runs a single iteration; each bitwise the
+    persistent kernel's results (ring of 878 markers, FP64)."""
+    case = wl.couette(256, n_corr=n_corr)
+    out = []
+    for phases in (0, 2):
+        lat = gpu_lattice(case, "fp64", None)
+        ibm.ibm_set_option(lat.h, ibm.IBM_OPT_IB_PHASES, phases)
+        lat.step(13)
+        out.append((lat.f, lat.resid, lat.bodies))
+        lat.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
